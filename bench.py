@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 RID recognizer on one text resident in HBM.
+
+One step = one pass of the whole hot path over the workload: ridfa_recognize_async (reach
+kernel over every chunk and interface slot, then the join kernel that yields the accept bit).
+Default workload: the 4 GiB ASCII record-line text against (TS,ID,FLOAT,WORD,IP\\n)*, cut into
+2^17 chunks.  The text (4 GiB) is larger than L2, so no flush is needed between steps.
+
+Printed (rank 0, one JSON line): value = input GB/s (device-timed, CUDA events on the launch
+stream), the all-states DFA comparator on the same text, the reach kernel's roofline against
+the measured HBM copy bandwidth, SM clocks sampled during the timed region, an end-to-end
+figure through the C ABI with the text copied from pinned host memory every step, and the
+oracle (Thompson state-set simulation, one host core) on a bounded sample as the CPU baseline.
+
+--impl reference times the oracle on the host cores instead (the comparison arm).
+With torchrun (N > 1) every rank recognises its own replica of the workload (weak scaling);
+there is no data-path collective.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input GB/s on 1 GB300 (RI-DFA vs all-states DFA), batched GB/s, served p99 ms"
+
+WORKLOADS = {
+    # name: (description, default bytes, default chunks)
+    "c3": ("ASCII record lines (TS,ID,FLOAT,WORD,IP\\n)*, literal field order", 4 << 30, 1 << 17),
+    "c3any": ("ASCII record lines, any field per column ((F)(,F)*\\n)*", 4 << 30, 1 << 17),
+    "c2": ("DNA motif RE with the {2,4} codon repeat, i.i.d. ACGT", 1 << 30, 1 << 16),
+    "c1": ("((A|C)*G(T|A)+C)*, walk on the minimal DFA", 1 << 20, 64),
+}
+
+
+def workload_re(name):
+    import textgen
+    return {"c3": textgen.C3_RE, "c3any": textgen.C3_RE_ANYFIELD,
+            "c2": textgen.C2_RE.replace("{20,60}", "{2,4}"), "c1": textgen.C1_RE}[name]
+
+
+def make_text(name, n, seed, device):
+    import torch
+
+    import textgen
+    if name in ("c3", "c3any"):
+        return textgen.c3_text_torch(n, seed, device=device)
+    if name == "c2":
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+        lut = torch.tensor(list(b"ACGT"), dtype=torch.uint8, device=device)
+        return lut[torch.randint(0, 4, (n,), generator=g, device=device)]
+    x = textgen.c1_text(n, seed)
+    return torch.from_numpy(x).to(device)
+
+
+def sample_text_numpy(name, n, seed):
+    import numpy as np
+
+    import textgen
+    if name in ("c3", "c3any"):
+        return textgen.c3_text(n, seed)
+    if name == "c2":
+        return textgen.c2_text(n, seed)
+    return textgen.c1_text(n, seed)
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, fl in enumerate(flags)
+                          if fl.lower() in ("active", "1", "yes")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(name, re_src, budget_s=12.0, seed=7):
+    """The oracle (Thompson state-set simulation, one core) on a bounded sample of the workload."""
+    from oracle.recognizer import SerialRecognizer
+    ser = SerialRecognizer(re_src)
+    n = 4 << 20
+    x = sample_text_numpy(name, n, seed)
+    t = time.perf_counter()
+    ser.accepts(x)
+    dt = time.perf_counter() - t
+    rate = x.size / max(dt, 1e-9)
+    n2 = int(min(256 << 20, max(n, rate * budget_s)))
+    if n2 > x.size:
+        x = sample_text_numpy(name, n2, seed + 1)
+        t = time.perf_counter()
+        ser.accepts(x)
+        dt = time.perf_counter() - t
+    return {"value": round(x.size / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{x.size} bytes of the same workload's text generator, one Thompson "
+                      f"state-set simulation pass ({dt:.1f} s)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    name = args.workload
+    re_src = workload_re(name)
+    from oracle.recognizer import SerialRecognizer
+    ser = SerialRecognizer(re_src)
+    per_step = 16 << 20
+    samples = [sample_text_numpy(name, per_step, 1000 + i) for i in range(2)]
+    for i in range(args.warmup):
+        ser.accepts(samples[i % 2])
+    t = time.perf_counter()
+    nbytes = 0
+    for i in range(args.steps):
+        x = samples[i % 2]
+        ser.accepts(x)
+        nbytes += x.size
+    dt = time.perf_counter() - t
+    v = nbytes / dt / 1e9
+    desc, _, _ = WORKLOADS[name]
+    line = {"metric": METRIC, "value": round(v, 6), "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{name}: {desc}", "sample_bytes_per_step": per_step},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(v, 6), "unit": "GB/s",
+                             "sample": f"{per_step} bytes per step of the workload's text generator"},
+            "e2e": {"value": round(v, 6), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--text-bytes", type=int, default=None)
+    ap.add_argument("--chunks", type=int, default=None)
+    ap.add_argument("--seed", type=int, default=0x5EED02)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-dfa", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2412_14975_gb300 as lib
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(dev))
+
+    name = args.workload
+    desc, n_default, c_default = WORKLOADS[name]
+    n_req = args.text_bytes or n_default
+    c = args.chunks or c_default
+    re_src = workload_re(name)
+    prog = lib.ridfa_compile(re_src)
+    info = prog.info
+    d_text = make_text(name, n_req, args.seed + rank, dev)
+    n = d_text.numel()
+    c = min(c, n)
+    stream = torch.cuda.current_stream()
+    d_accept = torch.zeros(1, dtype=torch.uint8, device=dev)
+
+    def step_rid():
+        lib.ridfa_recognize_async(prog, d_text, n, c, d_accept, stream=stream)
+
+    def step_dfa():
+        lib.ridfa_recognize_dfa_async(prog, d_text, n, c, d_accept, stream=stream)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms
+
+    # correctness guard of the timed configuration (device result vs the synchronous API)
+    acc = lib.ridfa_recognize(prog, d_text, n, c, stream=stream)
+
+    with ClockSampler(local) as clk:
+        ms = timed(step_rid, args.steps, args.warmup)
+    clocks = clk.summary()
+    value = world * n * args.steps / (ms / 1e3) / 1e9
+
+    dfa_value = None
+    if not args.no_dfa and info["n_dfa_states"] and info["n_dfa_states"] <= lib.RIDFA_MAX_SLOTS:
+        dacc = lib.ridfa_recognize_dfa(prog, d_text, n, c, stream=stream)
+        assert dacc == acc, "RID and all-states DFA disagree"
+        dms = timed(step_dfa, args.steps, args.warmup)
+        dfa_value = world * n * args.steps / (dms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (reach): events around its launch on the same stream
+    reach = []
+    joins = []
+    for _ in range(5):
+        lib.ridfa_recognize_async(prog, d_text, n, c, d_accept, tuning={"profile": 1}, stream=stream)
+        r, j = lib.ridfa_last_timings(prog)
+        reach.append(r)
+        joins.append(j)
+    reach_ms = statistics.median(reach)
+    join_ms = statistics.median(joins)
+    alg_bytes = n + c * info["k"] * 2 + c * 4
+    peaks, peak_kind = measured_peaks()
+    achieved = alg_bytes / (reach_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                "kernel": "rid_reach_kernel", "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(reach_ms, 4),
+                "join_ms": round(join_ms, 4)}
+
+    e2e = None
+    if not args.no_e2e:
+        h_text = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        h_text.copy_(d_text)
+        d_in = torch.empty_like(d_text)
+        for _ in range(2):
+            d_in.copy_(h_text, non_blocking=True)
+            lib.ridfa_recognize(prog, d_in, n, c, stream=stream)
+        k = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            d_in.copy_(h_text, non_blocking=True)
+            lib.ridfa_recognize(prog, d_in, n, c, stream=stream)   # includes the D2H of the bit
+        dt = time.perf_counter() - t0
+        e2e = {"value": round(n * k / dt / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": n,
+               "d2h_bytes_per_step": 1}
+        del h_text, d_in
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(name, re_src)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": {"workload": f"{name}: {desc}", "text_bytes": n, "n_chunks": c,
+                           "re": re_src, "nfa_states": info["n_nfa"], "ridfa_states": info["n_states"],
+                           "k": info["k"], "classes": info["n_classes"],
+                           "dfa_states": info["n_dfa_states"], "accept": bool(acc),
+                           "l2": "inputs larger than L2 (text > 129 MB), no flush",
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                "dfa_value": round(dfa_value, 3) if dfa_value else None,
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+                "gpu_launches": 2 * args.steps}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

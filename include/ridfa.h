@@ -1,0 +1,172 @@
+/*
+ * ridfa.h -- C ABI of the GB300 RID recognizer (reduced-interface DFA, speculative
+ * data-parallel recognition of regular texts).
+ *
+ * Method: A. Borsotti, L. Breveglieri, S. Crespi Reghizzi, A. Morzenti, "Minimizing
+ * speculation overhead in a parallel recognizer for regular texts" (arXiv 2412.14975).
+ *   - chunk automaton B (RI-DFA) built from the position NFA of the RE ............ Sec. 3.1
+ *   - chunking x = y_1 ... y_c, y_i non-empty ...................................... Sec. 2
+ *   - reach phase: lambda_i(a) = delta^B(a, y_i) for every interface state a ......... Sec. 3.2
+ *   - interface function if / if_min, join, acceptance PLAS_c n F^RID != {} ....... Sec. 3.2, 3.4
+ *   - all-states DFA comparator (the DFA variant of the classic algorithm) ........ Sec. 2, Fig. 2
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return an int status: RIDFA_OK (0) or a negative RIDFA_E_* code.  No C++
+ *     exception crosses this boundary.  ridfa_strerror() names a code.
+ *   - Text and chunk-map buffers passed as d_* are DEVICE pointers owned by the caller (e.g. the
+ *     data_ptr() of a CUDA tensor); h_* are host pointers owned by the caller.  The library owns
+ *     a ridfa_program (host tables, device tables and device scratch) until ridfa_free().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Device work
+ *     is enqueued on it; the *_async calls do not synchronise, the others do.
+ *   - Calls that use the same program must not run concurrently on different streams: the
+ *     program's device scratch is shared by its calls.
+ *   - Chunk boundaries are b_i = floor(i * len / n_chunks), chunk i = text[b_i, b_{i+1}), so
+ *     1 <= n_chunks <= len is required (every chunk non-empty, Sec. 2).
+ *   - Chunk maps are uint16 [n_chunks][k] (row-major); entry [i][a] is the state reached from
+ *     interface slot a over chunk i, or RIDFA_UNDEF (0xFFFF) when the run dies (the undefined
+ *     transition).  Row 0 is computed for every slot too, although the join uses only the slot
+ *     of {q0} there.
+ *
+ * RE dialect (bytes, full-text match): literal bytes; '.' any byte; [..] and [^..] with ranges;
+ * escapes \n \t \r \xHH and \c for any other c; ( ) grouping, () the empty word; postfix
+ * * + ? {m} {m,} {m,n}; concatenation; | (an empty alternative is the empty word).  Bounded
+ * repeats expand as r{m,n} = r^m (r(r(...r)?)?)? (n-m nested optional copies).
+ */
+#ifndef RIDFA_H
+#define RIDFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RIDFA_OK 0
+#define RIDFA_E_ARG (-1)             /* bad argument (NULL pointer, zero length where not allowed) */
+#define RIDFA_E_SYNTAX (-2)          /* the RE does not parse */
+#define RIDFA_E_TOO_MANY_STATES (-3) /* RI-DFA (or minimal DFA) exceeds max_states (<= 65534) */
+#define RIDFA_E_CHUNKS (-4)          /* n_chunks == 0 or n_chunks > len */
+#define RIDFA_E_NOMEM (-5)           /* host or device allocation failed */
+#define RIDFA_E_CUDA (-6)            /* a CUDA runtime call failed (no device, launch error, ...) */
+#define RIDFA_E_TIMEOUT (-7)         /* a bounded device wait gave up */
+#define RIDFA_E_BUSY (-8)            /* admission refused (device-memory budget) */
+#define RIDFA_E_UNSUPPORTED (-9)     /* e.g. more interface slots than the kernels support */
+#define RIDFA_E_NO_DFA (-10)         /* the program was compiled without the DFA comparator */
+#define RIDFA_E_STATE (-11)          /* internal consistency check failed on the device */
+
+#define RIDFA_UNDEF 0xFFFFu          /* chunk-map entry of a dead run */
+#define RIDFA_MAX_STATES 65534u
+#define RIDFA_MAX_SLOTS 256u         /* interface slots the device kernels support */
+
+typedef struct ridfa_program ridfa_program;
+
+typedef struct {
+    uint32_t minimize_interface; /* 1: Nerode delegation, if_min (Sec. 3.4); 0: I^B = all singletons */
+    uint32_t build_dfa;          /* 1: also build the minimal DFA for the all-states comparator */
+    uint32_t max_states;         /* cap on |P| and |Q_DFA|; 0 means RIDFA_MAX_STATES */
+} ridfa_compile_opts;
+
+typedef struct {
+    uint32_t n_nfa;          /* |Q_N| = number of positions + 1 (q0) */
+    uint32_t n_states;       /* |P|, states of the RI-DFA B (Sec. 3.1) */
+    uint32_t k;              /* interface slots |I^{B_min}| (= n_nfa without minimisation) */
+    uint32_t n_classes;      /* byte classes C (bytes read by exactly the same positions) */
+    uint32_t n_dfa_states;   /* |Q| of the minimal DFA (0 if not built) */
+    uint32_t q0_slot;        /* slot of {q0} */
+    uint64_t table_bytes;    /* device bytes of the RID tables */
+    uint64_t dfa_table_bytes;/* device bytes of the DFA tables (0 if not built) */
+} ridfa_info;
+
+typedef struct {
+    uint32_t chunks_per_lane; /* chunks each lane runs after convergence: 0 auto, 1, 2, 4 */
+    uint32_t block_threads;   /* threads per block of the reach kernel: 0 auto, 128..1024 */
+    uint32_t probe_interval;  /* bytes between convergence checks of the speculative runs: 0 auto */
+    uint32_t grid_blocks;     /* reach-kernel blocks: 0 auto (one wave on all SMs) */
+    uint32_t profile;         /* 1: record CUDA events around the reach and join launches on the
+                                 call's stream (read them back with ridfa_last_timings) */
+} ridfa_tuning;
+
+/* Compile `re` (re_len bytes, need not be NUL-terminated) on the host: position NFA, RI-DFA
+ * (incremental powerset N(q0) u N(q1) u ..., Sec. 3.1), Nerode partition and delegation
+ * (Sec. 3.4), byte classes, uint16 transition tables; optionally the minimal DFA.  Device tables
+ * are uploaded on first use by a recognize call (so this works without a GPU).
+ * opts may be NULL (minimize_interface = 1, build_dfa = 1, max_states = 65534).
+ * Errors: E_ARG, E_SYNTAX, E_TOO_MANY_STATES, E_NOMEM.  *out is set only on success. */
+int ridfa_compile(const char *re, size_t re_len, const ridfa_compile_opts *opts,
+                  ridfa_program **out);
+
+/* Release a program, its host tables and (on every device it was uploaded to) its device
+ * tables and scratch.  NULL is a no-op.  Must not race with calls using the program. */
+void ridfa_free(ridfa_program *prog);
+
+/* Sizes of the compiled automata.  Errors: E_ARG. */
+int ridfa_program_info(const ridfa_program *prog, ridfa_info *out);
+
+/* NFA states (0 = q0, p >= 1 = position p) contained in RI-DFA state `state` (the subset it
+ * stands for, Sec. 3.1), ascending, into out[0..cap).  *n_out = subset size.
+ * Errors: E_ARG (bad state or cap too small; *n_out still set). */
+int ridfa_state_set(const ridfa_program *prog, uint32_t state, uint32_t *out, uint32_t cap,
+                    uint32_t *n_out);
+
+/* out[a] = representative NFA state of interface slot a (a < k), ascending (Sec. 3.4: the
+ * lowest state of each language-equivalence class of singletons).  Errors: E_ARG. */
+int ridfa_slots(const ridfa_program *prog, uint32_t *out);
+
+/* out[q] = slot of the representative that NFA state q delegates to (q < n_nfa); this is the
+ * interface function if_min on singletons (Sec. 3.4).  Errors: E_ARG. */
+int ridfa_delegates(const ridfa_program *prog, uint32_t *out);
+
+/* Host copies of the tables the device kernels use.  which = 0: RI-DFA, 1: minimal DFA.
+ * trans: uint16 [(n+1) * n_classes] next state (row n and undefined moves = n, the dead
+ * state); classmap: uint8 [256]; final: uint8 [n] (1 = in F^RID / F).  Any pointer may be
+ * NULL.  Errors: E_ARG, E_NO_DFA. */
+int ridfa_export_tables(const ridfa_program *prog, int which, uint16_t *trans,
+                        uint8_t *classmap, uint8_t *final_flags);
+
+/* Recognize one text resident on the device (the RID: reach + join, Sec. 3.2).
+ * d_text: device pointer to len bytes (any alignment).  n_chunks: c, 1 <= c <= len.
+ * len == 0 is allowed with n_chunks == 0: the answer is whether the empty word is in L.
+ * tuning: NULL = automatic.  *h_accept = 1 if text in L(RE) else 0.  d_chunk_maps: NULL, or a
+ * device buffer of n_chunks * k uint16 that receives the chunk maps lambda_i.
+ * Synchronises `stream` before returning.
+ * Errors: E_ARG, E_CHUNKS, E_UNSUPPORTED (k > RIDFA_MAX_SLOTS), E_NOMEM, E_CUDA, E_STATE. */
+int ridfa_recognize(const ridfa_program *prog, const uint8_t *d_text, size_t len,
+                    uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *h_accept,
+                    uint16_t *d_chunk_maps, void *stream);
+
+/* As ridfa_recognize, but the accept byte goes to device memory d_accept (1 byte) and nothing
+ * is synchronised: the result is valid once `stream` reaches this point.  Device status
+ * (E_STATE) is then reported by the next call on the program, or by ridfa_last_status(). */
+int ridfa_recognize_async(const ridfa_program *prog, const uint8_t *d_text, size_t len,
+                          uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *d_accept,
+                          uint16_t *d_chunk_maps, void *stream);
+
+/* The all-states DFA comparator (the DFA variant of the classic algorithm, Sec. 2): every
+ * state of the minimal DFA is speculated on; chunk maps are [n_chunks][n_dfa_states].
+ * Same arguments and errors as ridfa_recognize, plus E_NO_DFA. */
+int ridfa_recognize_dfa(const ridfa_program *prog, const uint8_t *d_text, size_t len,
+                        uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *h_accept,
+                        uint16_t *d_chunk_maps, void *stream);
+
+int ridfa_recognize_dfa_async(const ridfa_program *prog, const uint8_t *d_text, size_t len,
+                              uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *d_accept,
+                              uint16_t *d_chunk_maps, void *stream);
+
+/* Synchronise `stream` and report the device status word of the program's last call
+ * (RIDFA_OK or E_STATE).  Errors: E_ARG, E_CUDA. */
+int ridfa_last_status(const ridfa_program *prog, void *stream);
+
+/* Device time of the last profiled call's reach kernel and join kernel, in milliseconds,
+ * from CUDA events recorded on that call's stream (tuning->profile = 1).  Waits for the
+ * events.  Errors: E_ARG (no profiled call yet), E_CUDA. */
+int ridfa_last_timings(const ridfa_program *prog, float *reach_ms, float *join_ms);
+
+/* Static text of a status code. */
+const char *ridfa_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIDFA_H */

@@ -1,0 +1,16 @@
+"""GB300 RID recognizer: Python binding of the C ABI in ``include/ridfa.h`` (libridfa.so).
+
+Argument marshalling only: every step of recognition runs in the library's sm_103a kernels.
+The binding loads ``libridfa.so`` from this directory and raises ImportError when it is missing
+(build it with ``python paper_2412_14975_gb300/build_lib.py``); there is no fallback.
+
+Device buffers may be given as CUDA tensors (anything with ``data_ptr()``) or as raw integer
+addresses; ``stream`` may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None
+(the current torch stream when torch is imported, else the legacy default stream).
+"""
+
+from ._lib import (RIDFA_MAX_SLOTS, RIDFA_MAX_STATES, RIDFA_UNDEF, Program, RidfaError,  # noqa: F401
+                   Tuning, lib_path, ridfa_compile, ridfa_delegates, ridfa_export_tables,
+                   ridfa_free, ridfa_last_status, ridfa_last_timings, ridfa_program_info, ridfa_recognize,
+                   ridfa_recognize_async, ridfa_recognize_dfa, ridfa_recognize_dfa_async,
+                   ridfa_slots, ridfa_state_set, ridfa_strerror, chunk_boundaries)

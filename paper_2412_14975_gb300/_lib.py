@@ -1,0 +1,253 @@
+"""ctypes declarations mirroring include/ridfa.h, with the same function names."""
+
+import ctypes
+import os
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libridfa.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"libridfa.so is not built ({_LIB_PATH}); run `python paper_2412_14975_gb300/build_lib.py` "
+        "(the recognizer has no CPU fallback)")
+
+_lib = ctypes.CDLL(_LIB_PATH)
+
+RIDFA_UNDEF = 0xFFFF
+RIDFA_MAX_STATES = 65534
+RIDFA_MAX_SLOTS = 256
+
+_c = ctypes
+_vp = _c.c_void_p
+_u32 = _c.c_uint32
+
+
+class CompileOpts(_c.Structure):
+    _fields_ = [("minimize_interface", _u32), ("build_dfa", _u32), ("max_states", _u32)]
+
+
+class Info(_c.Structure):
+    _fields_ = [("n_nfa", _u32), ("n_states", _u32), ("k", _u32), ("n_classes", _u32),
+                ("n_dfa_states", _u32), ("q0_slot", _u32), ("table_bytes", _c.c_uint64),
+                ("dfa_table_bytes", _c.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Tuning(_c.Structure):
+    _fields_ = [("chunks_per_lane", _u32), ("block_threads", _u32), ("probe_interval", _u32),
+                ("grid_blocks", _u32), ("profile", _u32)]
+
+
+def _decl(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_decl("ridfa_compile", _c.c_int, [_c.c_char_p, _c.c_size_t, _c.POINTER(CompileOpts), _c.POINTER(_vp)])
+_decl("ridfa_free", None, [_vp])
+_decl("ridfa_program_info", _c.c_int, [_vp, _c.POINTER(Info)])
+_decl("ridfa_state_set", _c.c_int, [_vp, _u32, _vp, _u32, _c.POINTER(_u32)])
+_decl("ridfa_slots", _c.c_int, [_vp, _vp])
+_decl("ridfa_delegates", _c.c_int, [_vp, _vp])
+_decl("ridfa_export_tables", _c.c_int, [_vp, _c.c_int, _vp, _vp, _vp])
+for _n in ("ridfa_recognize", "ridfa_recognize_async", "ridfa_recognize_dfa", "ridfa_recognize_dfa_async"):
+    _decl(_n, _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _c.POINTER(Tuning), _vp, _vp, _vp])
+_decl("ridfa_last_status", _c.c_int, [_vp, _vp])
+_decl("ridfa_strerror", _c.c_char_p, [_c.c_int])
+_decl("ridfa_last_timings", _c.c_int, [_vp, _c.POINTER(_c.c_float), _c.POINTER(_c.c_float)])
+
+
+class RidfaError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {ridfa_strerror(code)} ({code})")
+
+
+def lib_path():
+    return _LIB_PATH
+
+
+def ridfa_strerror(code):
+    return _lib.ridfa_strerror(int(code)).decode()
+
+
+def _check(code, where):
+    if code != 0:
+        raise RidfaError(code, where)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a device address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def chunk_boundaries(n, c):
+    """b_i = floor(i*n/c), i = 0..c (the chunking every entry point uses)."""
+    return [(i * n) // c for i in range(c + 1)]
+
+
+class Program:
+    """Owns one ridfa_program*; freed with ridfa_free when collected or closed."""
+
+    def __init__(self, handle, re_src):
+        self.handle = handle
+        self.re = re_src
+        self._info = ridfa_program_info(self)
+
+    @property
+    def info(self):
+        return self._info
+
+    def close(self):
+        if self.handle:
+            ridfa_free(self)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        if not self.handle:
+            raise ValueError("program is closed")
+        return self.handle
+
+
+def ridfa_compile(re_src, minimize_interface=True, build_dfa=True, max_states=0):
+    raw = re_src.encode("latin-1") if isinstance(re_src, str) else bytes(re_src)
+    opts = CompileOpts(int(bool(minimize_interface)), int(bool(build_dfa)), int(max_states))
+    h = _vp()
+    _check(_lib.ridfa_compile(raw, len(raw), _c.byref(opts), _c.byref(h)), "ridfa_compile")
+    return Program(h.value, re_src)
+
+
+def ridfa_free(prog):
+    _lib.ridfa_free(prog.handle)
+
+
+def ridfa_program_info(prog):
+    info = Info()
+    _check(_lib.ridfa_program_info(_vp(prog.handle), _c.byref(info)), "ridfa_program_info")
+    return info.as_dict()
+
+
+def ridfa_state_set(prog, state):
+    n = _u32()
+    _lib.ridfa_state_set(prog, int(state), None, 0, _c.byref(n))
+    out = np.zeros(max(1, n.value), dtype=np.uint32)
+    _check(_lib.ridfa_state_set(prog, int(state), out.ctypes.data, out.size, _c.byref(n)),
+           "ridfa_state_set")
+    return out[:n.value].copy()
+
+
+def ridfa_slots(prog):
+    out = np.zeros(max(1, prog.info["k"]), dtype=np.uint32)
+    _check(_lib.ridfa_slots(prog, out.ctypes.data), "ridfa_slots")
+    return out[:prog.info["k"]]
+
+
+def ridfa_delegates(prog):
+    out = np.zeros(prog.info["n_nfa"], dtype=np.uint32)
+    _check(_lib.ridfa_delegates(prog, out.ctypes.data), "ridfa_delegates")
+    return out
+
+
+def ridfa_export_tables(prog, which=0):
+    """(trans [(n+1), C] uint16, classmap [256] uint8, final [n] uint8) of the RI-DFA (0) or
+    the minimal DFA (1)."""
+    info = prog.info
+    n = info["n_states"] if which == 0 else info["n_dfa_states"]
+    if which == 1 and n == 0:
+        raise RidfaError(-10, "ridfa_export_tables")
+    trans = np.zeros((n + 1) * info["n_classes"], dtype=np.uint16)
+    cmap = np.zeros(256, dtype=np.uint8)
+    fin = np.zeros(max(1, n), dtype=np.uint8)
+    _check(_lib.ridfa_export_tables(prog, int(which), trans.ctypes.data, cmap.ctypes.data,
+                                    fin.ctypes.data), "ridfa_export_tables")
+    return trans.reshape(n + 1, info["n_classes"]), cmap, fin[:n]
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    if isinstance(t, Tuning):
+        return _c.byref(t)
+    return _c.byref(Tuning(t.get("chunks_per_lane", 0), t.get("block_threads", 0),
+                           t.get("probe_interval", 0), t.get("grid_blocks", 0),
+                           t.get("profile", 0)))
+
+
+def _recognize_sync(fn, name, prog, text, length, n_chunks, tuning, maps, stream):
+    acc = _c.c_uint8(0)
+    _check(fn(prog, _ptr(text), int(length), int(n_chunks), _tuning(tuning),
+              _c.addressof(acc), _ptr(maps), _stream(stream)), name)
+    return bool(acc.value)
+
+
+def _recognize_async(fn, name, prog, text, length, n_chunks, d_accept, tuning, maps, stream):
+    _check(fn(prog, _ptr(text), int(length), int(n_chunks), _tuning(tuning),
+              _ptr(d_accept), _ptr(maps), _stream(stream)), name)
+
+
+def ridfa_recognize(prog, d_text, length, n_chunks, tuning=None, d_chunk_maps=None, stream=None):
+    """Accept bit of the text (device buffer) by the RID; synchronises the stream."""
+    return _recognize_sync(_lib.ridfa_recognize, "ridfa_recognize", prog, d_text, length,
+                           n_chunks, tuning, d_chunk_maps, stream)
+
+
+def ridfa_recognize_async(prog, d_text, length, n_chunks, d_accept, tuning=None,
+                          d_chunk_maps=None, stream=None):
+    _recognize_async(_lib.ridfa_recognize_async, "ridfa_recognize_async", prog, d_text, length,
+                     n_chunks, d_accept, tuning, d_chunk_maps, stream)
+
+
+def ridfa_recognize_dfa(prog, d_text, length, n_chunks, tuning=None, d_chunk_maps=None, stream=None):
+    """Accept bit by the all-states minimal-DFA comparator; synchronises the stream."""
+    return _recognize_sync(_lib.ridfa_recognize_dfa, "ridfa_recognize_dfa", prog, d_text, length,
+                           n_chunks, tuning, d_chunk_maps, stream)
+
+
+def ridfa_recognize_dfa_async(prog, d_text, length, n_chunks, d_accept, tuning=None,
+                              d_chunk_maps=None, stream=None):
+    _recognize_async(_lib.ridfa_recognize_dfa_async, "ridfa_recognize_dfa_async", prog, d_text,
+                     length, n_chunks, d_accept, tuning, d_chunk_maps, stream)
+
+
+def ridfa_last_status(prog, stream=None):
+    code = _lib.ridfa_last_status(prog, _stream(stream))
+    return code
+
+
+def ridfa_last_timings(prog):
+    """(reach_ms, join_ms) of the last call made with tuning profile=1."""
+    a, b = _c.c_float(), _c.c_float()
+    _check(_lib.ridfa_last_timings(prog, _c.byref(a), _c.byref(b)), "ridfa_last_timings")
+    return a.value, b.value

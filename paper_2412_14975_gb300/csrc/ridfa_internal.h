@@ -1,0 +1,73 @@
+// Internal structures shared by the host compiler (ridfa_compile.cpp) and the device code
+// (ridfa_device.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ridfa.h"
+
+namespace ridfa {
+
+// One speculative automaton as the device sees it: the RI-DFA B with its interface
+// (Sec. 3.1-3.4) or the minimal DFA with every state initial (Sec. 2).
+struct HostAutomaton {
+    uint32_t n_states = 0;            // |P| (or |Q|); the dead state has id n_states
+    uint32_t n_classes = 0;           // byte classes C
+    uint32_t k = 0;                   // interface slots
+    uint32_t kw = 0;                  // 32-bit words per interface-set row: ceil(k / 32)
+    uint32_t q0_slot = 0;             // slot whose start state is {q0} (or the DFA start)
+    std::vector<uint16_t> trans;      // [(n_states + 1) * n_classes], dead row / moves = n_states
+    std::vector<uint8_t> classmap;    // [256]
+    std::vector<uint8_t> final_flag;  // [n_states]
+    std::vector<uint32_t> final_bits; // [ceil((n_states + 1) / 32)]
+    std::vector<uint32_t> ifmask;     // [(n_states + 1) * kw]: slots of if_min({p}); dead row = 0
+    std::vector<uint16_t> slot_state; // [k]: start state of each slot
+};
+
+// Device copy of one automaton (one per device it was uploaded to).
+struct DeviceAutomaton {
+    int device = -1;
+    uint16_t *trans = nullptr;
+    uint8_t *classmap = nullptr;
+    uint32_t *final_bits = nullptr;
+    uint32_t *ifmask = nullptr;
+    uint16_t *slot_state = nullptr;
+    size_t bytes = 0;
+};
+
+// Per-device scratch of a program: chunk maps when the caller passes none, per-chunk summaries,
+// the join's partial products, a block ticket, the status word and the accept byte.
+struct DeviceScratch {
+    int device = -1;
+    void *base = nullptr;
+    size_t bytes = 0;
+    uint8_t *h_accept_pinned = nullptr;
+    uint32_t *h_status_pinned = nullptr;
+    void *ev[3] = {nullptr, nullptr, nullptr};   // cudaEvent_t: before reach, before join, after
+    bool profiled = false;
+};
+
+}  // namespace ridfa
+
+struct ridfa_program {
+    std::string re;
+    uint32_t n_nfa = 0;
+    std::vector<std::vector<uint32_t>> state_sets;   // NFA states of each RI-DFA state
+    std::vector<uint32_t> slots;                      // representative NFA state per slot
+    std::vector<uint32_t> delegate_slot;              // NFA state -> slot of its representative
+    ridfa::HostAutomaton rid;
+    ridfa::HostAutomaton dfa;
+    bool has_dfa = false;
+    // device side (filled lazily by the device code)
+    mutable std::mutex mu;
+    mutable std::vector<ridfa::DeviceAutomaton> dev_rid, dev_dfa;
+    mutable std::vector<ridfa::DeviceScratch> scratch;
+};
+
+namespace ridfa {
+void release_device(const ridfa_program *prog);   // defined in the device code
+}

@@ -1,0 +1,184 @@
+"""GPU parity: the sm_103a reach + join kernels, called through the C ABI, against the oracle.
+
+Bit-exact everywhere (integer states): every chunk-map entry lambda_i(a) equals the oracle's
+delta^B({q_a}, y_i) (computed by position-set simulation, Lemma 1) under the shared numbering
+rule, and the accept bit equals the Thompson simulation.  The all-states DFA comparator is held
+to the same bar against the oracle's minimal DFA.
+"""
+import numpy as np
+import pytest
+
+import textgen
+from oracle.recognizer import RidOracle, SerialRecognizer
+from tests.gpu_util import run, to_device
+
+pytestmark = pytest.mark.gpu
+
+lib = pytest.importorskip("paper_2412_14975_gb300")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+_ORACLES = {}
+
+
+def oracle(re_src):
+    if re_src not in _ORACLES:
+        _ORACLES[re_src] = (RidOracle(re_src), SerialRecognizer(re_src))
+    return _ORACLES[re_src]
+
+
+def check(re_src, text, c, dfa_too=True, tuning=None, rows=None):
+    o, ser = oracle(re_src)
+    prog = lib.ridfa_compile(re_src)
+    n = text.size
+    d = to_device(text)
+    acc, maps = run(lib, prog, d, n, c, tuning=tuning)
+    want_acc = ser.accepts(text)
+    assert acc == want_acc, (re_src, n, c)
+    if rows is None and c * max(prog.info["k"], prog.info["n_dfa_states"]) > 20000:
+        rng = np.random.Generator(np.random.PCG64(c))
+        rows = sorted({0, 1, 2, c // 2, c - 2, c - 1} | set(rng.integers(0, c, 24).tolist()))
+    ids = range(c) if rows is None else rows
+    want = o.lambda_rows(text, c, ids)
+    for i in ids:
+        assert np.array_equal(maps[i], want[i]), (re_src, n, c, i, maps[i], want[i])
+    if dfa_too and prog.info["n_dfa_states"] <= lib.RIDFA_MAX_SLOTS:
+        dacc, dmaps = run(lib, prog, d, n, c, dfa=True, tuning=tuning)
+        assert dacc == want_acc
+        dwant = o.dfa_lambda_rows(text, c, ids)
+        for i in ids:
+            assert np.array_equal(dmaps[i], dwant[i]), (re_src, n, c, i)
+    return acc
+
+
+def test_config1_full_1mib_64_chunks():
+    x = textgen.c1_text(1 << 20, seed=0x5EED01)
+    assert check(textgen.C1_RE, x, 64)
+    m, _ = textgen.mutate(x, seed=0x5EED02, n_subs=1, alphabet=b"ACGT")
+    check(textgen.C1_RE, m, 64)
+
+
+SIZES = [1, 2, 3, 17, 31, 32, 33, 1000, 4097, 65536 + 7]
+
+
+@pytest.mark.parametrize("re_name", ["c1", "c3", "c3any", "c2_2_4", "regexp3", "regexp8"])
+def test_small_sizes_all_rows(re_name):
+    rng = np.random.Generator(np.random.PCG64(sum(map(ord, re_name))))
+    re_src = {"c1": textgen.C1_RE, "c3": textgen.C3_RE, "c3any": textgen.C3_RE_ANYFIELD,
+              "c2_2_4": textgen.C2_RE.replace("{20,60}", "{2,4}"),
+              "regexp3": textgen.regexp_family_re(3), "regexp8": textgen.regexp_family_re(8)}[re_name]
+    for n in SIZES:
+        if re_name == "c1":
+            x = textgen.c1_text(n, rng)[:n]
+        elif re_name.startswith("c3"):
+            x = textgen.c3_text(n, rng)[:n]
+        elif re_name.startswith("c2"):
+            x = textgen.c2_text(n, rng)
+        else:
+            x = textgen.regexp_family_text(n, rng)
+        for c in sorted({1, 2, 7, 31, 32, 33, 64, 1000, n}):
+            if c <= n:
+                check(re_src, x, c, dfa_too=(n <= 4097))
+        if n > 40:
+            y, _ = textgen.mutate(x, rng, n_subs=int(rng.integers(1, 4)))
+            check(re_src, y, min(n, 33))
+
+
+def test_random_res_random_texts():
+    rng = np.random.Generator(np.random.PCG64(0xC0FFEE))
+    done = 0
+    while done < 25:
+        node = textgen.random_re(rng, b"abcd", depth=int(rng.integers(2, 6)))
+        re_src = "(" + textgen.render(node) + ")*"
+        try:
+            prog = lib.ridfa_compile(re_src)
+        except lib.RidfaError:
+            continue
+        if prog.info["k"] > lib.RIDFA_MAX_SLOTS:
+            continue
+        parts = [textgen.sample_member(node, rng, soft_len=30) for _ in range(400)]
+        x = np.frombuffer(b"".join(parts), dtype=np.uint8)
+        if x.size < 8:
+            continue
+        if done % 2:
+            x, _ = textgen.mutate(x, rng, n_subs=1, alphabet=b"abcd")
+        for c in (1, 5, 64, min(x.size, 777)):
+            check(re_src, x, c, dfa_too=prog.info["n_dfa_states"] <= 256)
+        done += 1
+
+
+def test_empty_text_and_chunk_errors():
+    import torch
+    d = torch.zeros(16, dtype=torch.uint8, device="cuda:0")
+    for re_src, eps in [("a*", True), ("a+", False), ("()", True), ("(ab)*", True)]:
+        prog = lib.ridfa_compile(re_src)
+        assert lib.ridfa_recognize(prog, d, 0, 0) is eps
+        assert lib.ridfa_recognize_dfa(prog, d, 0, 0) is eps
+        with pytest.raises(lib.RidfaError) as e:
+            lib.ridfa_recognize(prog, d, 5, 6)
+        assert e.value.code == -4
+        with pytest.raises(lib.RidfaError) as e:
+            lib.ridfa_recognize(prog, d, 5, 0)
+        assert e.value.code == -4
+
+
+def test_out_of_alphabet_bytes_kill_runs():
+    x = np.frombuffer(b"ACGTTC" * 1000 + b"\x00" + b"ACG" * 100, dtype=np.uint8)
+    check(textgen.C1_RE, x, 50)
+    check(textgen.C1_RE, np.full(4096, 0xFF, dtype=np.uint8), 64)
+
+
+def _branches_re(nb):
+    xs = "ABCDEFGHIJKLMNOPQRSTUVWXYZ0123456789!#%&"
+    ys = "bcdefghijklmnopqrstuvwxyz<>=;:@$'\"^_`~,/"
+    return "(" + "|".join(f"{xs[i]}a*{ys[i]}" for i in range(nb)) + ")*", xs, ys
+
+
+@pytest.mark.parametrize("nb", [3, 20, 40])
+def test_many_distinct_end_states(nb):
+    """Chunks that end with several distinct live states (matrix join with m > 1, and the
+    sequential fallback when m > 32)."""
+    re_src, xs, ys = _branches_re(nb)
+    rng = np.random.Generator(np.random.PCG64(nb))
+    parts = []
+    for _ in range(30):
+        i = int(rng.integers(nb))
+        parts.append(xs[i] + "a" * int(rng.integers(0, 300)) + ys[i])
+    x = np.frombuffer("".join(parts).encode(), dtype=np.uint8)
+    for c in (3, 17, 100, 1000):
+        check(re_src, x, min(c, x.size), dfa_too=False)
+    y = x.copy()
+    y[x.size // 2] = ord(ys[0])
+    check(re_src, y, 100, dfa_too=False)
+
+
+def test_tuning_variants_agree():
+    x = textgen.c3_text(1 << 18, seed=77)
+    for t in [dict(probe_interval=1), dict(probe_interval=64), dict(block_threads=64),
+              dict(grid_blocks=1), dict(block_threads=128, grid_blocks=3)]:
+        check(textgen.C3_RE, x, 1000, dfa_too=True, tuning=t)
+
+
+def test_unminimized_interface_maps():
+    """With minimize_interface=0 every NFA state is a slot; maps still match the oracle."""
+    re_src = textgen.C1_RE
+    o = RidOracle(re_src, minimize=False)
+    prog = lib.ridfa_compile(re_src, minimize_interface=False)
+    x = textgen.c1_text(50_000, seed=3)
+    acc, maps = run(lib, prog, to_device(x), x.size, 77)
+    assert acc == SerialRecognizer(re_src).accepts(x)
+    want = o.lambda_rows(x, 77)
+    for i in range(77):
+        assert np.array_equal(maps[i], want[i])
+
+
+def test_c3_64mib_sampled_rows():
+    """A larger record-line text in the bench's launch shape (many chunks), sampled rows."""
+    x = textgen.c3_text(64 << 20, seed=0x5EED03)
+    c = 1 << 14
+    rows = sorted({0, 1, 2, c // 2, c - 2, c - 1} | set(
+        np.random.Generator(np.random.PCG64(1)).integers(0, c, 10).tolist()))
+    assert check(textgen.C3_RE, x, c, rows=rows)
+    y, _ = textgen.mutate(x, seed=5, n_subs=3)
+    check(textgen.C3_RE, y, c, rows=rows)

@@ -16,3 +16,4 @@ from .regex_ast import (Alt, Cat, Opt, Plus, Rep, Star, Sym, random_re, render,
 from .texts import (C1_RE, C2_RE, C3_RE, C3_RE_ANYFIELD, c1_min_dfa_table, c1_text,
                     c2_text, c3_text, dfa_walk, mutate, regexp_family_re,
                     regexp_family_text)  # noqa: F401
+from .texts_torch import c3_text_torch  # noqa: F401
