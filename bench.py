@@ -188,7 +188,7 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
@@ -198,6 +198,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dfa", action="store_true")
+    ap.add_argument("--table-mode", type=int, default=0,
+                    help="reach-kernel table layout (0 auto, 1 compact, 2 rep16, 3 rep32)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -231,9 +233,6 @@ def main():
     stream = torch.cuda.current_stream()
     d_accept = torch.zeros(1, dtype=torch.uint8, device=dev)
 
-    def step_rid():
-        lib.ridfa_recognize_async(prog, d_text, n, c, d_accept, stream=stream)
-
     def step_dfa():
         lib.ridfa_recognize_dfa_async(prog, d_text, n, c, d_accept, stream=stream)
 
@@ -262,7 +261,12 @@ def main():
     # correctness guard of the timed configuration (device result vs the synchronous API)
     acc = lib.ridfa_recognize(prog, d_text, n, c, stream=stream)
 
-    with ClockSampler(local) as clk:
+    tuning = {"table_mode": args.table_mode} if args.table_mode else None
+
+    def step_rid():
+        lib.ridfa_recognize_async(prog, d_text, n, c, d_accept, tuning=tuning, stream=stream)
+
+    with ClockSampler(local) as clk:      # sampling spans the warm-up and the timed steps
         ms = timed(step_rid, args.steps, args.warmup)
     clocks = clk.summary()
     value = world * n * args.steps / (ms / 1e3) / 1e9
@@ -278,7 +282,8 @@ def main():
     reach = []
     joins = []
     for _ in range(5):
-        lib.ridfa_recognize_async(prog, d_text, n, c, d_accept, tuning={"profile": 1}, stream=stream)
+        lib.ridfa_recognize_async(prog, d_text, n, c, d_accept,
+                                  tuning={"profile": 1, "table_mode": args.table_mode}, stream=stream)
         r, j = lib.ridfa_last_timings(prog)
         reach.append(r)
         joins.append(j)

@@ -79,12 +79,16 @@ typedef struct {
 } ridfa_info;
 
 typedef struct {
-    uint32_t chunks_per_lane; /* chunks each lane runs after convergence: 0 auto, 1, 2, 4 */
-    uint32_t block_threads;   /* threads per block of the reach kernel: 0 auto, 128..1024 */
+    uint32_t chunks_per_lane; /* reserved, must be 0 */
+    uint32_t block_threads;   /* threads per block of the reach kernel: 0 auto, a multiple of 32
+                                 up to 1024 (512 when k > 128) */
     uint32_t probe_interval;  /* bytes between convergence checks of the speculative runs: 0 auto */
     uint32_t grid_blocks;     /* reach-kernel blocks: 0 auto (one wave on all SMs) */
     uint32_t profile;         /* 1: record CUDA events around the reach and join launches on the
                                  call's stream (read them back with ridfa_last_timings) */
+    uint32_t table_mode;      /* reach-kernel table layout: 0 auto; 1 compact uint16 table;
+                                 2 lane-replicated 16-bit offsets; 3 lane-replicated 32-bit
+                                 offsets (E_ARG if the chosen layout does not fit) */
 } ridfa_tuning;
 
 /* Compile `re` (re_len bytes, need not be NUL-terminated) on the host: position NFA, RI-DFA

@@ -40,7 +40,7 @@ class Info(_c.Structure):
 
 class Tuning(_c.Structure):
     _fields_ = [("chunks_per_lane", _u32), ("block_threads", _u32), ("probe_interval", _u32),
-                ("grid_blocks", _u32), ("profile", _u32)]
+                ("grid_blocks", _u32), ("profile", _u32), ("table_mode", _u32)]
 
 
 def _decl(name, res, args):
@@ -202,7 +202,7 @@ def _tuning(t):
         return _c.byref(t)
     return _c.byref(Tuning(t.get("chunks_per_lane", 0), t.get("block_threads", 0),
                            t.get("probe_interval", 0), t.get("grid_blocks", 0),
-                           t.get("profile", 0)))
+                           t.get("profile", 0), t.get("table_mode", 0)))
 
 
 def _recognize_sync(fn, name, prog, text, length, n_chunks, tuning, maps, stream):

@@ -64,48 +64,162 @@ struct ReachArgs {
     uint32_t *dinfo;          // [c]: (m << 16) | min defined end state (0xFFFF if none)
     uint32_t *status;
     uint32_t probe;
-    int table_in_smem;
 };
 
-template <bool SMEM>
-struct Tab {
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Table lookup policies.  A run's state is kept in the policy's own encoding (`enc`); `id`
+// recovers the automaton state number.
+//
+// Plain: compact uint16 table [(n+1) * C] and uint8 class map, in shared memory (or global
+// memory when it does not fit).  Lanes gathering different entries may hit the same bank.
+struct LutPlain {
     const uint16_t *t;
     const uint8_t *cls;
     uint32_t C;
+    static size_t smem_bytes(const Automaton &A) { return 256 + static_cast<size_t>(A.n + 1) * A.C * 2; }
+    __device__ void setup(const Automaton &A, uint8_t *smem, bool table_in_smem) {
+        uint8_t *s_cls = smem;
+        uint16_t *s_t = reinterpret_cast<uint16_t *>(smem + 256);
+        for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_cls[i] = A.classmap[i];
+        if (table_in_smem)
+            for (uint32_t i = threadIdx.x; i < (A.n + 1) * A.C; i += blockDim.x) s_t[i] = A.trans[i];
+        t = table_in_smem ? s_t : A.trans;
+        cls = s_cls;
+        C = A.C;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id; }
+    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s; }
     __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return cls[b]; }
     __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return t[s * C + c]; }
 };
 
-template <int R, bool SMEM>
-__global__ void __launch_bounds__(256) rid_reach_kernel(ReachArgs p) {
+// Lane-replicated tables: every entry is stored 32 times, lane l's copy in bank l, so a warp's
+// 32 gathers are always one shared-memory wavefront whatever states and bytes the lanes hold.
+// Entries hold byte offsets, so a step is one add and one load:
+//   class table, 32-bit words: word (b * 32 + l) = class offset of byte b;
+//   Rep16 transition table, 16-bit halves: entry (s, c) at byte
+//       (s * Cp/2 + c/2) * 128 + l * 4 + (c & 1) * 2,   value = state offset s' * Cp * 64;
+//   Rep32 transition table, 32-bit words: entry (s, c) at word (s * C + c) * 32 + l,
+//       value = s' * C * 128.
+template <bool W16>
+struct LutRep {
+    uint32_t lc, lt;          // shared addresses of this lane's class / transition copies
+    uint32_t row;             // state offset stride
+    __host__ __device__ static uint32_t cpad(const Automaton &A) { return W16 ? (A.C + 1) & ~1u : A.C; }
+    static size_t smem_bytes(const Automaton &A) {
+        return 256 * 128 + static_cast<size_t>(A.n + 1) * cpad(A) * (W16 ? 64 : 128);
+    }
+    static bool fits16(const Automaton &A) {
+        return static_cast<uint64_t>(A.n) * cpad(A) * 64 + 128 * ((cpad(A) - 1) / 2) + 2 <= 0xFFFF;
+    }
+    __device__ __forceinline__ uint32_t cls_off(uint32_t c) const {
+        return W16 ? (c >> 1) * 128 + (c & 1) * 2 : c * 128;
+    }
+    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+        const uint32_t Cp = cpad(A);
+        row = W16 ? Cp * 64 : Cp * 128;
+        const uint32_t base_c = smem_addr(smem);
+        const uint32_t base_t = base_c + 256 * 128;
+        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x)
+            sts_u32(base_c + i * 4, cls_off(A.classmap[i >> 5]));
+        const uint32_t words = W16 ? (A.n + 1) * Cp / 2 : (A.n + 1) * Cp;
+        for (uint32_t i = threadIdx.x; i < words * 32; i += blockDim.x) {
+            const uint32_t w = i >> 5;
+            uint32_t v;
+            if (W16) {
+                const uint32_t s = (2 * w) / Cp, c0 = (2 * w) % Cp;
+                const uint32_t n0 = A.trans[s * A.C + c0];
+                const uint32_t n1 = (c0 + 1 < A.C) ? A.trans[s * A.C + c0 + 1] : A.n;
+                v = (n0 * row) | ((n1 * row) << 16);
+            } else {
+                v = A.trans[w] * row;
+            }
+            sts_u32(base_t + i * 4, v);
+        }
+        const uint32_t lane = threadIdx.x & 31;
+        lc = base_c + lane * 4;
+        lt = base_t + lane * 4;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id * row; }
+    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s / row; }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const {
+        return W16 ? lds_u16(lt + s + c) : lds_u32(lt + s + c);
+    }
+};
+
+// Chunk-map row of one chunk written by one lane: entries of alive slots get `val`.
+template <int R>
+__device__ __forceinline__ void write_row(uint16_t *row, uint32_t k, const uint32_t (&alive)[R],
+                                          uint16_t val) {
+    if ((k & 1) == 0) {
+        uint32_t *row32 = reinterpret_cast<uint32_t *>(row);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t m = alive[r];
+            for (uint32_t l = 0; l < 32; l += 2) {
+                const uint32_t a = r * 32 + l;
+                if (a >= k) break;
+                const uint32_t lo = ((m >> l) & 1) ? val : kUndef;
+                const uint32_t hi = ((m >> (l + 1)) & 1) ? val : kUndef;
+                row32[a >> 1] = lo | (hi << 16);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t m = alive[r];
+            for (uint32_t l = 0; l < 32; ++l) {
+                const uint32_t a = r * 32 + l;
+                if (a >= k) break;
+                row[a] = ((m >> l) & 1) ? val : kUndef;
+            }
+        }
+    }
+}
+
+template <int R, class LUT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int table_in_smem) {
     extern __shared__ __align__(16) uint8_t smem[];
     const Automaton &A = p.A;
-    uint8_t *s_cls = smem;
-    uint16_t *s_t = reinterpret_cast<uint16_t *>(smem + 256);
-    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_cls[i] = A.classmap[i];
-    const uint32_t tab_n = (A.n + 1) * A.C;
-    if (SMEM)
-        for (uint32_t i = threadIdx.x; i < tab_n; i += blockDim.x) s_t[i] = A.trans[i];
+    LUT T;
+    T.setup(A, smem, table_in_smem != 0);
     __syncthreads();
-    Tab<SMEM> T{SMEM ? s_t : A.trans, s_cls, A.C};
 
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t dead = A.n;
+    const uint32_t dead = T.enc(A.n);
     const uint64_t n_tasks = (static_cast<uint64_t>(p.c) + 31) / 32;
     const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
 
     // slot start states of this lane (slot a = r*32 + lane)
     uint32_t start_state[R];
+    uint32_t start_live = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        uint32_t a = r * 32 + lane;
-        start_state[r] = a < A.k ? A.slot_state[a] : dead;
+        const uint32_t a = r * 32 + lane;
+        start_state[r] = a < A.k ? T.enc(A.slot_state[a]) : dead;
+        if (r * 32 < static_cast<int>(A.k)) start_live |= 1u << r;
     }
 
     for (uint64_t task = warp0; task < n_tasks; task += n_warps) {
         const uint64_t chunk0 = task * 32;
-        // what this lane must still do for chunk chunk0 + lane
         uint64_t my_pos = 0;
         uint32_t my_state = dead;
         uint32_t my_alive[R];
@@ -122,6 +236,7 @@ __global__ void __launch_bounds__(256) rid_reach_kernel(ReachArgs p) {
             uint32_t s[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) s[r] = start_state[r];
+            uint32_t live_regs = start_live;       // registers holding at least one live run
             uint64_t pos = beg;
             bool converged = false;
             uint32_t conv_state = dead;
@@ -130,16 +245,20 @@ __global__ void __launch_bounds__(256) rid_reach_kernel(ReachArgs p) {
                 for (; pos < stop; ++pos) {
                     const uint32_t c = T.cls_of(__ldg(p.text + pos));
 #pragma unroll
-                    for (int r = 0; r < R; ++r) s[r] = T.next(s[r], c);
+                    for (int r = 0; r < R; ++r)
+                        if (live_regs & (1u << r)) s[r] = T.next(s[r], c);
                 }
-                // convergence check: all live runs in one state?
+                // convergence: are all live runs in one state?  (dead runs are dropped)
                 uint32_t lo = 0xFFFFFFFFu, hi = 0;
+                live_regs = 0;
 #pragma unroll
-                for (int r = 0; r < R; ++r)
+                for (int r = 0; r < R; ++r) {
+                    if (__any_sync(kFull, s[r] != dead)) live_regs |= 1u << r;
                     if (s[r] != dead) {
                         lo = min(lo, s[r]);
                         hi = max(hi, s[r]);
                     }
+                }
                 lo = __reduce_min_sync(kFull, lo);
                 hi = __reduce_max_sync(kFull, hi);
                 if (lo == 0xFFFFFFFFu || lo == hi) {
@@ -153,7 +272,7 @@ __global__ void __launch_bounds__(256) rid_reach_kernel(ReachArgs p) {
                 // hand the single surviving run to lane j
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    uint32_t b = __ballot_sync(kFull, s[r] != dead);
+                    const uint32_t b = __ballot_sync(kFull, s[r] != dead);
                     if (lane == j) my_alive[r] = b;
                 }
                 if (lane == j) {
@@ -165,8 +284,8 @@ __global__ void __launch_bounds__(256) rid_reach_kernel(ReachArgs p) {
                 // finished in the speculative phase: write the row (coalesced) and D_i's size
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    uint32_t a = r * 32 + lane;
-                    if (a < A.k) row[a] = s[r] == dead ? kUndef : static_cast<uint16_t>(s[r]);
+                    const uint32_t a = r * 32 + lane;
+                    if (a < A.k) row[a] = s[r] == dead ? kUndef : static_cast<uint16_t>(T.id(s[r]));
                 }
                 uint32_t cnt = 0, first = kUndef, cur = 0;
                 bool more = true;
@@ -179,7 +298,7 @@ __global__ void __launch_bounds__(256) rid_reach_kernel(ReachArgs p) {
                     if (v == 0xFFFFFFFFu) {
                         more = false;
                     } else {
-                        if (cnt == 0) first = v;
+                        if (cnt == 0) first = T.id(v);
                         cur = v;
                         if (++cnt > kMaxD) more = false;
                     }
@@ -209,31 +328,25 @@ __global__ void __launch_bounds__(256) rid_reach_kernel(ReachArgs p) {
             while (pos + 16 <= end && s != dead) {
                 const uint4 v = __ldg(reinterpret_cast<const uint4 *>(t + pos));
                 const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                uint32_t cl[16];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
 #pragma unroll
-                    for (int bb = 0; bb < 4; ++bb) s = T.next(s, T.cls_of((w[q] >> (8 * bb)) & 0xFF));
-                }
+                for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
                 pos += 16;
             }
             while (pos < end && s != dead) {
                 s = T.next(s, T.cls_of(__ldg(t + pos)));
                 ++pos;
             }
-            uint16_t *row = p.maps + ch * A.k;
-            const uint16_t val = s == dead ? kUndef : static_cast<uint16_t>(s);
             bool any = false;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint32_t m = my_alive[r];
-                any |= m != 0;
-                for (uint32_t l = 0; l < 32; ++l) {
-                    const uint32_t a = r * 32 + l;
-                    if (a < A.k) row[a] = ((m >> l) & 1) ? val : kUndef;
-                }
-            }
+            for (int r = 0; r < R; ++r) any |= my_alive[r] != 0;
+            const uint32_t sid = T.id(s);
+            const uint16_t val = s == dead ? kUndef : static_cast<uint16_t>(sid);
+            write_row<R>(p.maps + ch * A.k, A.k, my_alive, val);
             const bool live = any && s != dead;
-            p.dinfo[ch] = live ? ((1u << 16) | s) : static_cast<uint32_t>(kUndef);
+            p.dinfo[ch] = live ? ((1u << 16) | sid) : static_cast<uint32_t>(kUndef);
         }
     }
 }
@@ -423,18 +536,32 @@ __global__ void __launch_bounds__(kJoinThreads) rid_join_kernel(JoinArgs p) {
         s_last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!s_last || tid != 0) return;
+    if (!s_last) return;
     __threadfence();
-    // ---- last block: compose the block products in order, then head and acceptance
+    // ---- last block: compose the block products in order (256 at a time, tree in shared
+    // memory), then the head lambda_1(q0) and the acceptance test on D_c
     Prod tot;
     tot.nrows = 0xFFFFFFFFu;
-    for (uint32_t b = 0; b < gridDim.x; ++b) {
-        const volatile uint32_t *q = p.partials + static_cast<uint64_t>(b) * (1 + kMaxD);
+    for (uint32_t base = 0; base < gridDim.x; base += blockDim.x) {
         Prod x;
-        x.nrows = q[0];
-        for (uint32_t r = 0; r < kMaxD; ++r) x.rows[r] = q[1 + r];
-        compose(tot, x);
+        x.nrows = 0xFFFFFFFFu;
+        if (base + tid < gridDim.x) {
+            const volatile uint32_t *q = p.partials + static_cast<uint64_t>(base + tid) * (1 + kMaxD);
+            x.nrows = q[0];
+            if (x.nrows != 0xFFFFFFFFu)
+                for (uint32_t r = 0; r < x.nrows; ++r) x.rows[r] = q[1 + r];
+        }
+        __syncthreads();
+        s_prod[tid] = x;
+        __syncthreads();
+        for (uint32_t stride = 1; stride < blockDim.x; stride *= 2) {
+            if ((tid % (2 * stride)) == 0 && tid + stride < blockDim.x) compose(s_prod[tid], s_prod[tid + stride]);
+            __syncthreads();
+        }
+        if (tid == 0) compose(tot, s_prod[0]);
+        __syncthreads();
     }
+    if (tid != 0) return;
     *p.ticket = 0;   // ready for the next launch on this scratch
     const uint16_t v0 = p.maps[A.q0_slot];
     uint8_t acc = 0;
@@ -558,25 +685,43 @@ int smem_optin_limit() {
     return v;
 }
 
-template <int R, bool SMEM>
-cudaError_t launch_reach_t(const ReachArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
-    auto kern = rid_reach_kernel<R, SMEM>;
+enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3 };
+
+template <int R>
+constexpr int block_cap() { return R <= 4 ? 1024 : 512; }
+
+// Launch (or, with per_sm != nullptr, size) one instantiation of the reach kernel.
+template <int R, class LUT>
+cudaError_t reach_one(const ReachArgs &a, int table_in_smem, int grid, int block, size_t smem,
+                      cudaStream_t st, int *per_sm) {
+    auto kern = rid_reach_kernel<R, LUT, block_cap<R>()>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, block, smem, st>>>(a);
+    if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, block, smem);
+    kern<<<grid, block, smem, st>>>(a, table_in_smem);
     return cudaGetLastError();
 }
 
-template <bool SMEM>
-cudaError_t launch_reach_r(int R, const ReachArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
+template <class LUT>
+cudaError_t reach_r(int R, const ReachArgs &a, int tis, int grid, int block, size_t smem,
+                    cudaStream_t st, int *per_sm) {
     switch (R) {
-        case 1: return launch_reach_t<1, SMEM>(a, grid, block, smem, st);
-        case 2: return launch_reach_t<2, SMEM>(a, grid, block, smem, st);
-        case 4: return launch_reach_t<4, SMEM>(a, grid, block, smem, st);
-        default: return launch_reach_t<8, SMEM>(a, grid, block, smem, st);
+        case 1: return reach_one<1, LUT>(a, tis, grid, block, smem, st, per_sm);
+        case 2: return reach_one<2, LUT>(a, tis, grid, block, smem, st, per_sm);
+        case 4: return reach_one<4, LUT>(a, tis, grid, block, smem, st, per_sm);
+        default: return reach_one<8, LUT>(a, tis, grid, block, smem, st, per_sm);
+    }
+}
+
+cudaError_t reach_dispatch(uint32_t mode, int R, const ReachArgs &a, int tis, int grid, int block,
+                           size_t smem, cudaStream_t st, int *per_sm) {
+    switch (mode) {
+        case kModeRep16: return reach_r<LutRep<true>>(R, a, tis, grid, block, smem, st, per_sm);
+        case kModeRep32: return reach_r<LutRep<false>>(R, a, tis, grid, block, smem, st, per_sm);
+        default: return reach_r<LutPlain>(R, a, tis, grid, block, smem, st, per_sm);
     }
 }
 
@@ -615,10 +760,13 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t c = n_chunks;
     const uint64_t nbound = c - 1;
-    uint32_t per_thread = static_cast<uint32_t>(std::max<uint64_t>(1, (nbound + static_cast<uint64_t>(kJoinThreads) * sms * 2 - 1) /
-                                                                         (static_cast<uint64_t>(kJoinThreads) * sms * 2)));
-    uint32_t join_blocks = static_cast<uint32_t>(std::max<uint64_t>(1, (nbound + static_cast<uint64_t>(kJoinThreads) * per_thread - 1) /
-                                                                           (static_cast<uint64_t>(kJoinThreads) * per_thread)));
+    const uint64_t per_block_max = 1024;
+    uint32_t per_thread = static_cast<uint32_t>(std::max<uint64_t>(
+        1, (nbound + static_cast<uint64_t>(kJoinThreads) * per_block_max - 1) /
+               (static_cast<uint64_t>(kJoinThreads) * per_block_max)));
+    uint32_t join_blocks = static_cast<uint32_t>(std::max<uint64_t>(
+        1, (nbound + static_cast<uint64_t>(kJoinThreads) * per_thread - 1) /
+               (static_cast<uint64_t>(kJoinThreads) * per_thread)));
     const Layout L = layout_for(c, H.k, d_maps_user == nullptr, join_blocks);
     DeviceScratch *S = scratch_for(P, dev, L.total, &err);
     if (!S) return err;
@@ -636,34 +784,39 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     if (e != cudaSuccess) return cuda_fail(e);
 
     // ---- reach
-    ReachArgs ra{A, d_text, len, n_chunks, maps, dinfo, status, 8, 0};
+    ReachArgs ra{A, d_text, len, n_chunks, maps, dinfo, status, 8};
     if (tuning && tuning->probe_interval) ra.probe = tuning->probe_interval;
     const int R = H.k <= 32 ? 1 : H.k <= 64 ? 2 : H.k <= 128 ? 4 : 8;
-    const size_t tab_bytes = static_cast<size_t>(H.n_states + 1) * H.n_classes * 2;
-    const size_t smem_full = 256 + tab_bytes;
-    const bool in_smem = smem_full <= static_cast<size_t>(smem_optin_limit()) - 1024;
-    const int block = (tuning && tuning->block_threads) ? static_cast<int>(tuning->block_threads) : 256;
-    if (block < 32 || block > 256 || block % 32) return RIDFA_E_ARG;
+    const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024;
+    // table layout: lane-replicated 16-bit offsets, else 32-bit offsets, else the compact table
+    uint32_t mode = tuning ? tuning->table_mode : 0;
+    const size_t rep16 = LutRep<true>::smem_bytes(A), rep32 = LutRep<false>::smem_bytes(A);
+    if (mode == 0)
+        mode = (LutRep<true>::fits16(A) && rep16 <= limit) ? kModeRep16
+               : (rep32 <= limit) ? kModeRep32 : kModePlain;
+    if (mode == kModeRep16 && !(LutRep<true>::fits16(A) && rep16 <= limit)) return RIDFA_E_ARG;
+    if (mode == kModeRep32 && rep32 > limit) return RIDFA_E_ARG;
+    if (mode < kModePlain || mode > kModeRep32) return RIDFA_E_ARG;
+    const size_t plain_bytes = LutPlain::smem_bytes(A);
+    const int tis = (mode == kModePlain && plain_bytes <= limit) ? 1 : 0;
+    const size_t smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : (tis ? plain_bytes : 256);
+    const int cap = R <= 4 ? 1024 : 512;
+    int block = (tuning && tuning->block_threads) ? static_cast<int>(tuning->block_threads)
+                                                  : (mode == kModePlain ? 256 : cap);
+    if (block < 32 || block > cap || block % 32) return RIDFA_E_ARG;
     const uint64_t tasks = (c + 31) / 32;
     int grid;
     if (tuning && tuning->grid_blocks) {
         grid = static_cast<int>(tuning->grid_blocks);
     } else {
         int per_sm = 0;
-        if (in_smem) {
-            switch (R) {
-                case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rid_reach_kernel<1, true>, block, smem_full); break;
-                case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rid_reach_kernel<2, true>, block, smem_full); break;
-                case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rid_reach_kernel<4, true>, block, smem_full); break;
-                default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rid_reach_kernel<8, true>, block, smem_full); break;
-            }
-        }
-        per_sm = std::max(per_sm, 1);
+        e = reach_dispatch(mode, R, ra, tis, 0, block, smem, st, &per_sm);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (per_sm < 1) return RIDFA_E_UNSUPPORTED;
         const uint64_t warps_per_block = block / 32;
         const uint64_t need = (tasks + warps_per_block - 1) / warps_per_block;
         grid = static_cast<int>(std::min<uint64_t>(need, static_cast<uint64_t>(sms) * per_sm));
     }
-    ra.table_in_smem = in_smem ? 1 : 0;
     const bool prof = tuning && tuning->profile;
     if (prof) {
         for (auto &ev : S->ev)
@@ -675,8 +828,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
             }
         cudaEventRecord(static_cast<cudaEvent_t>(S->ev[0]), st);
     }
-    e = in_smem ? launch_reach_r<true>(R, ra, grid, block, smem_full, st)
-                : launch_reach_r<false>(R, ra, grid, block, 256, st);
+    e = reach_dispatch(mode, R, ra, tis, grid, block, smem, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
     if (prof) cudaEventRecord(static_cast<cudaEvent_t>(S->ev[1]), st);
 

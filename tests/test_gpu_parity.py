@@ -153,11 +153,29 @@ def test_many_distinct_end_states(nb):
     check(re_src, y, 100, dfa_too=False)
 
 
-def test_tuning_variants_agree():
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_tuning_variants_agree(mode):
+    """Every table layout (compact, lane-replicated 16/32-bit) and launch shape gives the same
+    bit-exact maps."""
     x = textgen.c3_text(1 << 18, seed=77)
     for t in [dict(probe_interval=1), dict(probe_interval=64), dict(block_threads=64),
-              dict(grid_blocks=1), dict(block_threads=128, grid_blocks=3)]:
+              dict(grid_blocks=1), dict(block_threads=128, grid_blocks=3),
+              dict(block_threads=1024), dict()]:
+        t["table_mode"] = mode
         check(textgen.C3_RE, x, 1000, dfa_too=True, tuning=t)
+    y = textgen.c1_text(1 << 16, seed=78)
+    check(textgen.C1_RE, y, 300, tuning=dict(table_mode=mode))
+    re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
+    z = textgen.c2_text(1 << 16, seed=79)
+    # 424 states x 5 classes: only the compact layout fits (16-bit offsets overflow, the 32-bit
+    # replicated table exceeds shared memory), so the automatic choice must pick it
+    check(re2, z, 200, tuning=dict(table_mode=1 if mode == 1 else 0), dfa_too=False)
+    prog = lib.ridfa_compile(re2)
+    d = to_device(z)
+    for bad in (2, 3):
+        with pytest.raises(lib.RidfaError) as e:
+            lib.ridfa_recognize(prog, d, z.size, 200, tuning=dict(table_mode=bad))
+        assert e.value.code == -1
 
 
 def test_unminimized_interface_maps():
