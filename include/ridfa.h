@@ -54,10 +54,12 @@ extern "C" {
 #define RIDFA_E_UNSUPPORTED (-9)     /* e.g. more interface slots than the kernels support */
 #define RIDFA_E_NO_DFA (-10)         /* the program was compiled without the DFA comparator */
 #define RIDFA_E_STATE (-11)          /* internal consistency check failed on the device */
+#define RIDFA_E_TOO_LARGE (-12)      /* tables + scratch exceed RIDFA_NOALLOC_SCRATCH_BYTES */
 
 #define RIDFA_UNDEF 0xFFFFu          /* chunk-map entry of a dead run */
 #define RIDFA_MAX_STATES 65534u
 #define RIDFA_MAX_SLOTS 256u         /* interface slots the device kernels support */
+#define RIDFA_NOALLOC_SCRATCH_BYTES (4u << 20) /* fixed device array of ridfa_recognize_noalloc */
 
 typedef struct ridfa_program ridfa_program;
 
@@ -156,6 +158,30 @@ int ridfa_recognize_dfa(const ridfa_program *prog, const uint8_t *d_text, size_t
 int ridfa_recognize_dfa_async(const ridfa_program *prog, const uint8_t *d_text, size_t len,
                               uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *d_accept,
                               uint16_t *d_chunk_maps, void *stream);
+
+/* The paper has no counterpart to this call.  It is the RID path (the same reach and join
+ * kernels as ridfa_recognize_async) for callers that must not allocate device memory while they
+ * run: cudaMalloc can stall every stream of the device and can fail when another framework's
+ * caching allocator already holds the memory, so latency-bound services, and plug-ins whose host
+ * application owns all device allocations, need a recognize call that allocates nothing.
+ * No cudaMalloc, cudaFree or other allocating routine is called.  The program's tables and all
+ * kernel scratch live in one fixed device array of RIDFA_NOALLOC_SCRATCH_BYTES (4 MiB) that
+ * every GPU loading the library holds until the process exits.
+ *   d_text: device pointer to len bytes; n_chunks: 1 <= c <= len (len == 0 needs c == 0).
+ *   d_accept: device byte, receives 1 if the text is in L(RE) else 0 (written on `stream`).
+ *   d_chunk_maps: REQUIRED device buffer of n_chunks * k uint16 (the chunk maps, as in
+ *   ridfa_recognize).  Nothing is synchronised.
+ * Limits: the tables plus 4 bytes per chunk plus about 133 KiB of join scratch must fit in the
+ * array, otherwise RIDFA_E_TOO_LARGE and nothing is launched.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call copies the program's tables into
+ * the array and clears the counters the join needs; the array keeps the last call's contents.
+ * Calls that overlap on the GPU (on different streams, from different threads or programs) use
+ * the same array and race: serialise them.
+ * Errors: E_ARG, E_CHUNKS, E_UNSUPPORTED (k > RIDFA_MAX_SLOTS), E_TOO_LARGE, E_CUDA. */
+int ridfa_recognize_noalloc(const ridfa_program *prog, const uint8_t *d_text, size_t len,
+                            uint32_t n_chunks, uint8_t *d_accept, uint16_t *d_chunk_maps,
+                            void *stream);
 
 /* Synchronise `stream` and report the device status word of the program's last call
  * (RIDFA_OK or E_STATE).  Errors: E_ARG, E_CUDA. */

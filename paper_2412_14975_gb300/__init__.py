@@ -9,7 +9,8 @@ addresses; ``stream`` may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` int
 (the current torch stream when torch is imported, else the legacy default stream).
 """
 
-from ._lib import (RIDFA_MAX_SLOTS, RIDFA_MAX_STATES, RIDFA_UNDEF, Program, RidfaError,  # noqa: F401
+from ._lib import (RIDFA_MAX_SLOTS, RIDFA_MAX_STATES, RIDFA_NOALLOC_SCRATCH_BYTES,  # noqa: F401
+                   RIDFA_UNDEF, Program, RidfaError, ridfa_recognize_noalloc,
                    Tuning, lib_path, ridfa_compile, ridfa_delegates, ridfa_export_tables,
                    ridfa_free, ridfa_last_status, ridfa_last_timings, ridfa_program_info, ridfa_recognize,
                    ridfa_recognize_async, ridfa_recognize_dfa, ridfa_recognize_dfa_async,

@@ -19,6 +19,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 RIDFA_UNDEF = 0xFFFF
 RIDFA_MAX_STATES = 65534
 RIDFA_MAX_SLOTS = 256
+RIDFA_NOALLOC_SCRATCH_BYTES = 4 << 20
 
 _c = ctypes
 _vp = _c.c_void_p
@@ -60,6 +61,7 @@ _decl("ridfa_export_tables", _c.c_int, [_vp, _c.c_int, _vp, _vp, _vp])
 for _n in ("ridfa_recognize", "ridfa_recognize_async", "ridfa_recognize_dfa", "ridfa_recognize_dfa_async"):
     _decl(_n, _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _c.POINTER(Tuning), _vp, _vp, _vp])
 _decl("ridfa_last_status", _c.c_int, [_vp, _vp])
+_decl("ridfa_recognize_noalloc", _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _vp, _vp, _vp])
 _decl("ridfa_strerror", _c.c_char_p, [_c.c_int])
 _decl("ridfa_last_timings", _c.c_int, [_vp, _c.POINTER(_c.c_float), _c.POINTER(_c.c_float)])
 
@@ -251,3 +253,12 @@ def ridfa_last_timings(prog):
     a, b = _c.c_float(), _c.c_float()
     _check(_lib.ridfa_last_timings(prog, _c.byref(a), _c.byref(b)), "ridfa_last_timings")
     return a.value, b.value
+
+
+def ridfa_recognize_noalloc(prog, d_text, length, n_chunks, d_accept, d_chunk_maps, stream=None):
+    """RID path that allocates no device memory: tables and scratch live in the library's fixed
+    RIDFA_NOALLOC_SCRATCH_BYTES device array; d_chunk_maps (n_chunks * k uint16) is required.
+    Asynchronous on `stream`; overlapping calls share the array and must be serialised."""
+    _check(_lib.ridfa_recognize_noalloc(prog, _ptr(d_text), int(length), int(n_chunks),
+                                        _ptr(d_accept), _ptr(d_chunk_maps), _stream(stream)),
+           "ridfa_recognize_noalloc")

@@ -792,6 +792,8 @@ extern "C" const char *ridfa_strerror(int code) {
         case RIDFA_E_UNSUPPORTED: return "unsupported size (too many interface slots)";
         case RIDFA_E_NO_DFA: return "program has no DFA comparator";
         case RIDFA_E_STATE: return "device consistency check failed";
+        case RIDFA_E_TOO_LARGE:
+            return "tables and scratch exceed the fixed no-allocation array (RIDFA_NOALLOC_SCRATCH_BYTES)";
         default: return "unknown status";
     }
 }

@@ -39,6 +39,7 @@ constexpr uint32_t kStatusWide = 1u;      // some chunk has > 32 distinct end st
 constexpr uint32_t kStatusBad = 2u;       // a device consistency check failed
 constexpr int kMaxD = 32;                 // distinct end states handled by the matrix join
 constexpr int kJoinThreads = 256;
+static_assert(kPartialWords == 1 + kMaxD, "join partial layout");
 
 struct Automaton {            // device view of one automaton
     const uint16_t *trans;    // [(n+1) * C]
@@ -876,6 +877,49 @@ void release_device(const ridfa_program *P) {
     }
     cudaSetDevice(cur);
     (void)cudaGetLastError();
+}
+
+int launch_with_buffers(const HostAutomaton &H, const PreparedBuffers &B, const uint8_t *d_text,
+                        uint64_t len, uint32_t n_chunks, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t c = n_chunks;
+    const uint64_t nbound = c - 1;
+    const uint64_t per_thread = std::max<uint64_t>(
+        1, (nbound + static_cast<uint64_t>(kJoinThreads) * kMaxJoinBlocks - 1) /
+               (static_cast<uint64_t>(kJoinThreads) * kMaxJoinBlocks));
+    const uint32_t join_blocks = static_cast<uint32_t>(std::max<uint64_t>(
+        1, (nbound + kJoinThreads * per_thread - 1) / (kJoinThreads * per_thread)));
+    Automaton A{B.trans, B.classmap, B.final_bits, B.ifmask, B.slot_state,
+                H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+    ReachArgs ra{A, d_text, len, n_chunks, B.maps, B.dinfo, B.status, 8};
+    const int R = H.k <= 32 ? 1 : H.k <= 64 ? 2 : H.k <= 128 ? 4 : 8;
+    const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024;
+    const size_t rep16 = LutRep<true>::smem_bytes(A), rep32 = LutRep<false>::smem_bytes(A);
+    const uint32_t mode = (LutRep<true>::fits16(A) && rep16 <= limit) ? kModeRep16
+                          : (rep32 <= limit) ? kModeRep32 : kModePlain;
+    const size_t plain_bytes = LutPlain::smem_bytes(A);
+    const int tis = (mode == kModePlain && plain_bytes <= limit) ? 1 : 0;
+    const size_t smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : (tis ? plain_bytes : 256);
+    const int block = mode == kModePlain ? 256 : (R <= 4 ? 1024 : 512);
+    int per_sm = 0;
+    e = reach_dispatch(mode, R, ra, tis, 0, block, smem, st, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (per_sm < 1) return RIDFA_E_UNSUPPORTED;
+    const uint64_t tasks = (c + 31) / 32;
+    const uint64_t need = (tasks + block / 32 - 1) / (block / 32);
+    const int grid = static_cast<int>(std::min<uint64_t>(need, static_cast<uint64_t>(sms) * per_sm));
+    e = reach_dispatch(mode, R, ra, tis, grid, block, smem, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e);
+    JoinArgs ja{A, n_chunks, B.maps, B.dinfo, B.status, B.partials, B.ticket, B.accept,
+                static_cast<uint32_t>(per_thread)};
+    rid_join_kernel<<<join_blocks, kJoinThreads, 0, st>>>(ja);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? RIDFA_OK : cuda_fail(e);
 }
 
 }  // namespace ridfa

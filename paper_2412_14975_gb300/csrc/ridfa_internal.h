@@ -70,4 +70,27 @@ struct ridfa_program {
 
 namespace ridfa {
 void release_device(const ridfa_program *prog);   // defined in the device code
+
+// Device buffers supplied by the caller of launch_with_buffers: the automaton's tables and every
+// piece of scratch the reach and join kernels use.  Nothing is allocated by the launch.
+struct PreparedBuffers {
+    const uint16_t *trans;
+    const uint8_t *classmap;
+    const uint32_t *final_bits;
+    const uint32_t *ifmask;
+    const uint16_t *slot_state;
+    uint16_t *maps;        // [c][k]
+    uint32_t *dinfo;       // [c]
+    uint32_t *partials;    // [kMaxJoinBlocks][33]
+    uint32_t *ticket;      // zero before the launch
+    uint32_t *status;      // zero before the launch
+    uint8_t *accept;
+};
+constexpr uint32_t kMaxJoinBlocks = 1024;
+constexpr uint32_t kPartialWords = 33;
+
+// Enqueue the reach and join kernels of the RID path (automatic tuning) on `stream`, on buffers
+// that are already resident.  Returns a RIDFA_* status; performs no allocation.
+int launch_with_buffers(const HostAutomaton &H, const PreparedBuffers &B, const uint8_t *d_text,
+                        uint64_t len, uint32_t n_chunks, void *stream);
 }
