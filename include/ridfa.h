@@ -91,6 +91,12 @@ typedef struct {
     uint32_t table_mode;      /* reach-kernel table layout: 0 auto; 1 compact uint16 table;
                                  2 lane-replicated 16-bit offsets; 3 lane-replicated 32-bit
                                  offsets (E_ARG if the chosen layout does not fit) */
+    uint32_t text_path;       /* how the converged runs read the text: 0 auto; 1 each lane's own
+                                 16-byte global loads; 2 per-lane bulk copies (cp.async.bulk)
+                                 into a shared-memory ring; 3 warp-cooperative coalesced loads
+                                 staged in shared memory; 4 the same with two chunks per lane,
+                                 interleaved.  2, 3 and 4 need a 16-byte-aligned d_text
+                                 (E_ARG otherwise) */
 } ridfa_tuning;
 
 /* Compile `re` (re_len bytes, need not be NUL-terminated) on the host: position NFA, RI-DFA
@@ -191,6 +197,17 @@ int ridfa_last_status(const ridfa_program *prog, void *stream);
  * from CUDA events recorded on that call's stream (tuning->profile = 1).  Waits for the
  * events.  Errors: E_ARG (no profiled call yet), E_CUDA. */
 int ridfa_last_timings(const ridfa_program *prog, float *reach_ms, float *join_ms);
+
+/* Roofline microbenchmarks (diagnostics; the paper has no counterpart).  Both allocate a 4-byte
+ * sink and synchronise the current device.
+ * ridfa_bench_smem_gather: the reach kernel's converged step alone -- per text byte one
+ *   lane-private shared-memory gather for the byte's class and one for the next state (dependent
+ *   on the previous state) -- on every SM with 1024 threads, `iters` bytes per thread.  Returns
+ *   the rate in text bytes per second (*ms_out: the timed launch).  Errors: E_ARG, E_CUDA.
+ * ridfa_bench_hbm_read: streaming read of `bytes` of a 16-byte-aligned device buffer with 16-byte
+ *   loads; returns bytes per second.  Errors: E_ARG, E_CUDA. */
+int ridfa_bench_smem_gather(uint32_t iters, double *bytes_per_s, double *ms_out);
+int ridfa_bench_hbm_read(const uint8_t *d_buf, size_t bytes, double *bytes_per_s, double *ms_out);
 
 /* Static text of a status code. */
 const char *ridfa_strerror(int code);

@@ -11,6 +11,7 @@ addresses; ``stream`` may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` int
 
 from ._lib import (RIDFA_MAX_SLOTS, RIDFA_MAX_STATES, RIDFA_NOALLOC_SCRATCH_BYTES,  # noqa: F401
                    RIDFA_UNDEF, Program, RidfaError, ridfa_recognize_noalloc,
+                   ridfa_bench_hbm_read, ridfa_bench_smem_gather,
                    Tuning, lib_path, ridfa_compile, ridfa_delegates, ridfa_export_tables,
                    ridfa_free, ridfa_last_status, ridfa_last_timings, ridfa_program_info, ridfa_recognize,
                    ridfa_recognize_async, ridfa_recognize_dfa, ridfa_recognize_dfa_async,

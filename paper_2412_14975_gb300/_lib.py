@@ -41,7 +41,8 @@ class Info(_c.Structure):
 
 class Tuning(_c.Structure):
     _fields_ = [("chunks_per_lane", _u32), ("block_threads", _u32), ("probe_interval", _u32),
-                ("grid_blocks", _u32), ("profile", _u32), ("table_mode", _u32)]
+                ("grid_blocks", _u32), ("profile", _u32), ("table_mode", _u32),
+                ("text_path", _u32)]
 
 
 def _decl(name, res, args):
@@ -62,6 +63,8 @@ for _n in ("ridfa_recognize", "ridfa_recognize_async", "ridfa_recognize_dfa", "r
     _decl(_n, _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _c.POINTER(Tuning), _vp, _vp, _vp])
 _decl("ridfa_last_status", _c.c_int, [_vp, _vp])
 _decl("ridfa_recognize_noalloc", _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _vp, _vp, _vp])
+_decl("ridfa_bench_smem_gather", _c.c_int, [_u32, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)])
+_decl("ridfa_bench_hbm_read", _c.c_int, [_vp, _c.c_size_t, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)])
 _decl("ridfa_strerror", _c.c_char_p, [_c.c_int])
 _decl("ridfa_last_timings", _c.c_int, [_vp, _c.POINTER(_c.c_float), _c.POINTER(_c.c_float)])
 
@@ -204,7 +207,7 @@ def _tuning(t):
         return _c.byref(t)
     return _c.byref(Tuning(t.get("chunks_per_lane", 0), t.get("block_threads", 0),
                            t.get("probe_interval", 0), t.get("grid_blocks", 0),
-                           t.get("profile", 0), t.get("table_mode", 0)))
+                           t.get("profile", 0), t.get("table_mode", 0), t.get("text_path", 0)))
 
 
 def _recognize_sync(fn, name, prog, text, length, n_chunks, tuning, maps, stream):
@@ -262,3 +265,17 @@ def ridfa_recognize_noalloc(prog, d_text, length, n_chunks, d_accept, d_chunk_ma
     _check(_lib.ridfa_recognize_noalloc(prog, _ptr(d_text), int(length), int(n_chunks),
                                         _ptr(d_accept), _ptr(d_chunk_maps), _stream(stream)),
            "ridfa_recognize_noalloc")
+
+
+def ridfa_bench_smem_gather(iters=1 << 16):
+    """Text bytes per second of the converged step alone (two lane-private gathers per byte)."""
+    r, ms = _c.c_double(), _c.c_double()
+    _check(_lib.ridfa_bench_smem_gather(int(iters), _c.byref(r), _c.byref(ms)), "ridfa_bench_smem_gather")
+    return r.value
+
+
+def ridfa_bench_hbm_read(d_buf, nbytes):
+    """Streaming-read bytes per second over a 16-byte-aligned device buffer."""
+    r, ms = _c.c_double(), _c.c_double()
+    _check(_lib.ridfa_bench_hbm_read(_ptr(d_buf), int(nbytes), _c.byref(r), _c.byref(ms)), "ridfa_bench_hbm_read")
+    return r.value

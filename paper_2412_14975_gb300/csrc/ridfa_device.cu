@@ -84,6 +84,79 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Text staging for the converged phase (TMA path): every lane streams its own chunk through a
+// ring of kStages windows of kWin bytes in shared memory, filled by 1-D bulk copies
+// (cp.async.bulk) that complete on one mbarrier per warp and stage.  A lane's window buffers
+// are kLaneStride bytes apart, so the 16-byte reads of 8 consecutive lanes fall in 8 different
+// bank groups (stride 48 = 3 granules, and 3 is odd).
+constexpr uint32_t kWin = 128;
+constexpr uint32_t kStages = 2;
+constexpr uint32_t kLaneStride = 144;
+// per-warp ring + barriers, rounded to 16 bytes so every warp's ring starts 16-byte aligned
+// (bulk-copy destinations must be)
+constexpr uint32_t kWarpStageBytes = (kStages * 32 * kLaneStride + kStages * 8 + 15) & ~15u;
+static_assert(kWarpStageBytes % 16 == 0 && (kStages * 32 * kLaneStride) % 16 == 0 && kLaneStride % 16 == 0,
+              "bulk-copy destinations must stay 16-byte aligned");
+constexpr uint32_t kStatusTimeout = 4u;   // a bounded wait on a copy gave up
+// text paths of the converged phase
+constexpr int kPathGlobal = 0;   // each lane: 16-byte global loads of its own chunk
+constexpr int kPathBulk = 1;     // each lane: 1-D bulk copies into a shared-memory ring
+constexpr int kPathCoop = 2;     // the warp: coalesced loads of 8 chunks' windows per instruction
+constexpr int kPathCoop2 = 3;    // the same with two chunks per lane, interleaved
+// cooperative path: one 64-byte window per chunk of the warp; granule g of chunk j's window sits
+// at 16-byte unit 4j + (g ^ ((j >> 1) & 3)), so both the stores (lanes write 4 granules of 2
+// chunks per 8-lane phase) and the owners' 16-byte reads (8 chunks, one granule each) are
+// conflict-free
+constexpr uint32_t kCoopWin = 64;
+constexpr uint32_t kCoopBufBytes = 32 * kCoopWin;          // one round: a window per chunk
+constexpr uint32_t kWarpCoopBytes = 2 * kCoopBufBytes;     // double-buffered
+
+__device__ __forceinline__ void cp_async_16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ uint32_t coop_unit(uint32_t j, uint32_t g) { return 4 * j + (g ^ ((j >> 1) & 3)); }
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t tx) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P1;\n\t}"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ uint4 lds_v4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u8(uint32_t addr) {
+    uint16_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v;
+}
+
 // Table lookup policies.  A run's state is kept in the policy's own encoding (`enc`); `id`
 // recovers the automaton state number.
 //
@@ -195,13 +268,26 @@ __device__ __forceinline__ void write_row(uint16_t *row, uint32_t k, const uint3
     }
 }
 
-template <int R, class LUT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int table_in_smem) {
-    extern __shared__ __align__(16) uint8_t smem[];
+template <int R, class LUT, int BLOCK, int PATH>
+__global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int table_in_smem,
+                                                            uint32_t staging_offset) {
+    extern __shared__ __align__(128) uint8_t smem[];
     const Automaton &A = p.A;
     LUT T;
     T.setup(A, smem, table_in_smem != 0);
+    // per-warp staging ring and its mbarriers (TMA path only)
+    const uint32_t warp_in_block = threadIdx.x >> 5;
+    const uint32_t stg_base = smem_addr(smem) + staging_offset +
+                              warp_in_block * (PATH == kPathCoop ? kWarpCoopBytes : kWarpStageBytes);
+    const uint32_t bar_base = stg_base + kStages * 32 * kLaneStride;
+    if (PATH == kPathBulk) {
+        if ((threadIdx.x & 31) == 0)
+            for (uint32_t st = 0; st < kStages; ++st) mbar_init(bar_base + st * 8, 1);
+        fence_mbar_init();
+    }
     __syncthreads();
+    uint32_t wctr = 0, rctr = 0;     // bulk-copy windows issued / consumed by this warp
+    bool failed = false;
 
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t dead = T.enc(A.n);
@@ -316,25 +402,172 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
         }
 
         // ---------------- converged phase: each lane finishes its own chunk's single run
+        uint64_t pos = my_pos, end = 0;
+        uint32_t s = my_state;
+        if (my_pending) end = chunk_begin(chunk0 + lane + 1, p.len, p.c);
+        if (PATH == kPathCoop && __any_sync(kFull, my_pending)) {
+            // windows [wb + 64r, +64) of each chunk (wb = the 16-byte boundary at or below the
+            // resume position); bytes at or past `lim` (len rounded down to 16) use plain loads.
+            // Lane l copies granule (l & 3) of the windows of chunks (l >> 2) + 8u, u = 0..3, with
+            // cp.async (L2 -> shared memory, no register or L1 round trip): 8 chunks' windows per
+            // instruction, one round ahead, double-buffered.
+            const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
+            const uint64_t stop = min(end, lim);
+            const uint64_t wb = pos & ~static_cast<uint64_t>(15);
+            const uint32_t nwin = (my_pending && wb < stop)
+                                      ? static_cast<uint32_t>((stop - wb + kCoopWin - 1) / kCoopWin) : 0;
+            const uint32_t g = lane & 3;
+            const uint32_t max_win = __reduce_max_sync(kFull, nwin);
+            auto issue = [&](uint32_t r) {
+                const uint32_t buf = stg_base + (r & 1) * kCoopBufBytes;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = u * 8 + (lane >> 2);        // chunk whose granule g this lane copies
+                    const uint64_t a = __shfl_sync(kFull, wb, j) + static_cast<uint64_t>(kCoopWin) * r + 16 * g;
+                    const uint32_t nw = __shfl_sync(kFull, nwin, j);
+                    if (r < nw && a + 16 <= lim) cp_async_16(buf + 16 * coop_unit(j, g), p.text + a);
+                }
+                cp_async_commit();
+            };
+            issue(0);
+            const uint32_t sw = (lane >> 1) & 3;
+            for (uint32_t r = 0; r < max_win; ++r) {
+                if (r + 1 < max_win) issue(r + 1);
+                else cp_async_commit();               // keep one group per round
+                cp_async_wait1();                     // this lane's copies of round r have landed
+                __syncwarp();                         // ... and every other lane's
+                const uint64_t ws = wb + static_cast<uint64_t>(kCoopWin) * r;
+                if (r < nwin && s != dead) {
+                    const uint32_t sb = stg_base + (r & 1) * kCoopBufBytes + 64 * lane;
+                    const uint64_t lo = max(pos, ws), hi = min(stop, ws + kCoopWin);
+                    if (lo == ws && hi == ws + kCoopWin) {
+#pragma unroll
+                        for (uint32_t q16 = 0; q16 < kCoopWin / 16; ++q16) {
+                            const uint4 x = lds_v4(sb + 16 * (q16 ^ sw));
+                            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+                            uint32_t cl[16];
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
+                        }
+                    } else {
+                        for (uint64_t q = lo; q < hi; ++q) {
+                            const uint32_t o = static_cast<uint32_t>(q - ws);
+                            s = T.next(s, T.cls_of(lds_u8(sb + 16 * ((o >> 4) ^ sw) + (o & 15))));
+                        }
+                    }
+                    pos = hi;
+                }
+                __syncwarp();                         // buffer (r & 1) is refilled next round
+            }
+            cp_async_wait0();
+            __syncwarp();
+        }
+        if (PATH == kPathBulk) {
+            if (__any_sync(kFull, my_pending) && !failed) {
+                // windows [ws0 + kWin*j, +kWin) of the 16-byte-aligned text; bytes at or past
+                // `lim` (the text length rounded down to 16) are left to plain loads below
+                const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
+                const uint64_t ws0 = pos & ~static_cast<uint64_t>(15);
+                const uint64_t stop = min(end, lim);
+                uint32_t j_issue = 0, j_read = 0;
+                auto issue = [&]() {
+                    const uint32_t stage = wctr % kStages;
+                    const uint32_t bar = bar_base + stage * 8;
+                    const uint64_t ws = ws0 + static_cast<uint64_t>(kWin) * j_issue;
+                    uint32_t bytes = 0;
+                    if (my_pending && s != dead && ws < stop)
+                        bytes = static_cast<uint32_t>(min(static_cast<uint64_t>(kWin), lim - ws));
+                    const uint32_t total = __reduce_add_sync(kFull, bytes);
+                    if (lane == 0) mbar_arrive_expect_tx(bar, total);
+                    __syncwarp();
+                    if (bytes)
+                        bulk_copy_g2s(stg_base + (stage * 32 + lane) * kLaneStride, p.text + ws, bytes, bar);
+                    ++wctr;
+                    ++j_issue;
+                };
+                auto wait_stage = [&]() -> bool {
+                    const uint32_t bar = bar_base + (rctr % kStages) * 8;
+                    const uint32_t parity = (rctr / kStages) & 1;
+                    for (uint32_t it = 0; it < kSpinLimit; ++it)
+                        if (__all_sync(kFull, mbar_try_wait(bar, parity))) {
+                            ++rctr;
+                            return true;
+                        }
+                    return false;
+                };
+                for (uint32_t i = 0; i < kStages; ++i) issue();
+                for (;;) {
+                    const uint64_t ws = ws0 + static_cast<uint64_t>(kWin) * j_read;
+                    const bool have = my_pending && s != dead && ws < stop;
+                    if (!__any_sync(kFull, have)) break;
+                    const uint32_t stage = rctr % kStages;
+                    if (!wait_stage()) {
+                        failed = true;
+                        break;
+                    }
+                    if (have) {
+                        const uint32_t sb = stg_base + (stage * 32 + lane) * kLaneStride;
+                        const uint64_t lo = max(pos, ws), hi = min(stop, ws + kWin);
+                        if (lo == ws && hi == ws + kWin) {
+#pragma unroll
+                            for (uint32_t g = 0; g < kWin / 16; ++g) {
+                                const uint4 v = lds_v4(sb + 16 * g);
+                                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                                uint32_t cl[16];
+#pragma unroll
+                                for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
+#pragma unroll
+                                for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
+                            }
+                        } else {
+                            for (uint64_t q = lo; q < hi; ++q)
+                                s = T.next(s, T.cls_of(lds_u8(sb + static_cast<uint32_t>(q - ws))));
+                        }
+                        pos = hi;
+                    }
+                    ++j_read;
+                    __syncwarp();
+                    fence_proxy_async_smem();
+                    issue();
+                }
+                // windows issued past the last one read carry no bytes; consume their phases
+                while (!failed && rctr < wctr)
+                    if (!wait_stage()) failed = true;
+                if (failed) {
+                    // a copy did not land within the spin limit: report it, give the copies
+                    // still in flight one more bounded wait each, and leave
+                    if (lane == 0) atomicOr(p.status, kStatusTimeout);
+                    while (rctr < wctr) {
+                        const uint32_t bar = bar_base + (rctr % kStages) * 8;
+                        const uint32_t parity = (rctr / kStages) & 1;
+                        for (uint32_t it = 0; it < kSpinLimit && !__all_sync(kFull, mbar_try_wait(bar, parity)); ++it) {
+                        }
+                        ++rctr;
+                    }
+                    return;
+                }
+            }
+        }
         if (my_pending) {
             const uint64_t ch = chunk0 + lane;
-            const uint64_t end = chunk_begin(ch + 1, p.len, p.c);
-            uint64_t pos = my_pos;
-            uint32_t s = my_state;
             const uint8_t *t = p.text;
-            while (pos < end && (reinterpret_cast<uintptr_t>(t + pos) & 15)) {
-                s = T.next(s, T.cls_of(__ldg(t + pos)));
-                ++pos;
-            }
-            while (pos + 16 <= end && s != dead) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(t + pos));
-                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-                uint32_t cl[16];
+            if (PATH == kPathGlobal) {
+                while (pos < end && (reinterpret_cast<uintptr_t>(t + pos) & 15)) {
+                    s = T.next(s, T.cls_of(__ldg(t + pos)));
+                    ++pos;
+                }
+                while (pos + 16 <= end && s != dead) {
+                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(t + pos));
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                    uint32_t cl[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
+                    for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
-                pos += 16;
+                    for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
+                    pos += 16;
+                }
             }
             while (pos < end && s != dead) {
                 s = T.next(s, T.cls_of(__ldg(t + pos)));
@@ -348,6 +581,289 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
             write_row<R>(p.maps + ch * A.k, A.k, my_alive, val);
             const bool live = any && s != dead;
             p.dinfo[ch] = live ? ((1u << 16) | sid) : static_cast<uint32_t>(kUndef);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ reach, two chains per lane
+// Speculative phase of one chunk by the whole warp (lanes = runs).  Returns true when the live
+// runs merged into one state before the chunk end; then *out_pos / *out_state hold where and
+// what, and alive[] the ballots of the slots still alive (the same in every lane).  Otherwise the
+// chunk finished here: its map row and D_i summary are written and false is returned.
+template <int R, class LUT>
+__device__ __forceinline__ bool speculate_chunk(const ReachArgs &p, const LUT &T, uint64_t ch,
+                                                uint32_t lane, const uint32_t (&start_state)[R],
+                                                uint32_t start_live, uint32_t dead, uint64_t *out_pos,
+                                                uint32_t *out_state, uint32_t (&alive)[R]) {
+    const Automaton &A = p.A;
+    const uint64_t beg = chunk_begin(ch, p.len, p.c);
+    const uint64_t end = chunk_begin(ch + 1, p.len, p.c);
+    uint32_t s[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) s[r] = start_state[r];
+    uint32_t live_regs = start_live;
+    uint64_t pos = beg;
+    bool converged = false;
+    uint32_t conv_state = dead;
+    while (pos < end) {
+        const uint64_t stop = min(end, pos + p.probe);
+        for (; pos < stop; ++pos) {
+            const uint32_t c = T.cls_of(__ldg(p.text + pos));
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (live_regs & (1u << r)) s[r] = T.next(s[r], c);
+        }
+        uint32_t lo = 0xFFFFFFFFu, hi = 0;
+        live_regs = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (__any_sync(kFull, s[r] != dead)) live_regs |= 1u << r;
+            if (s[r] != dead) {
+                lo = min(lo, s[r]);
+                hi = max(hi, s[r]);
+            }
+        }
+        lo = __reduce_min_sync(kFull, lo);
+        hi = __reduce_max_sync(kFull, hi);
+        if (lo == 0xFFFFFFFFu || lo == hi) {
+            converged = true;
+            conv_state = (lo == 0xFFFFFFFFu) ? dead : lo;
+            break;
+        }
+    }
+    if (converged && pos < end && conv_state != dead) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) alive[r] = __ballot_sync(kFull, s[r] != dead);
+        *out_pos = pos;
+        *out_state = conv_state;
+        return true;
+    }
+    uint16_t *row = p.maps + ch * A.k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t a = r * 32 + lane;
+        if (a < A.k) row[a] = s[r] == dead ? kUndef : static_cast<uint16_t>(T.id(s[r]));
+    }
+    uint32_t cnt = 0, first = kUndef, cur = 0;
+    bool more = true;
+    while (more) {
+        uint32_t v = 0xFFFFFFFFu;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (s[r] != dead && (cnt == 0 || s[r] > cur)) v = min(v, s[r]);
+        v = __reduce_min_sync(kFull, v);
+        if (v == 0xFFFFFFFFu) {
+            more = false;
+        } else {
+            if (cnt == 0) first = T.id(v);
+            cur = v;
+            if (++cnt > kMaxD) more = false;
+        }
+    }
+    if (lane == 0) {
+        if (cnt > kMaxD) {
+            p.dinfo[ch] = (0xFFu << 16) | first;
+            atomicOr(p.status, kStatusWide);
+        } else {
+            p.dinfo[ch] = (cnt << 16) | first;
+        }
+    }
+    return false;
+}
+
+// 16 transitions of one chain over one 16-byte granule held in shared memory.
+template <class LUT>
+__device__ __forceinline__ uint32_t run_granule(const LUT &T, uint32_t s, uint32_t addr) {
+    const uint4 x = lds_v4(addr);
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+    uint32_t cl[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
+    return s;
+}
+
+// The same for two independent chains, interleaved so their lookups overlap.
+template <class LUT>
+__device__ __forceinline__ void run_granule2(const LUT &T, uint32_t &s0, uint32_t a0, uint32_t &s1,
+                                             uint32_t a1) {
+    const uint4 x = lds_v4(a0), y = lds_v4(a1);
+    const uint32_t w0[4] = {x.x, x.y, x.z, x.w}, w1[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t c0[8], c1[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int b = h * 8 + q;
+            c0[q] = T.cls_of((w0[b >> 2] >> (8 * (b & 3))) & 0xFF);
+            c1[q] = T.cls_of((w1[b >> 2] >> (8 * (b & 3))) & 0xFF);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            s0 = T.next(s0, c0[q]);
+            s1 = T.next(s1, c1[q]);
+        }
+    }
+}
+
+// Cooperative text path with two chunks per lane.  A warp owns 64 consecutive chunks: lane l
+// finishes chunks l and 32 + l after the speculative phase, interleaving the two runs.  Each
+// round the warp loads one 32-byte window of each of its 64 chunks with coalesced 16-byte loads
+// (16 chunks' windows per instruction, two lanes per window), one round ahead, into a shared
+// buffer whose windows sit 48 bytes apart (3 granules, odd: conflict-free 16-byte reads).
+constexpr uint32_t kC2Win = 32;
+constexpr uint32_t kC2Stride = 48;
+constexpr uint32_t kWarpCoop2Bytes = 64 * kC2Stride;
+
+template <int R, class LUT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) rid_reach2_kernel(ReachArgs p, int table_in_smem,
+                                                             uint32_t staging_offset) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const Automaton &A = p.A;
+    LUT T;
+    T.setup(A, smem, table_in_smem != 0);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t stg = smem_addr(smem) + staging_offset + (threadIdx.x >> 5) * kWarpCoop2Bytes;
+    const uint32_t dead = T.enc(A.n);
+    const uint64_t n_tasks = (static_cast<uint64_t>(p.c) + 63) / 64;
+    const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
+
+    uint32_t start_state[R];
+    uint32_t start_live = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t a = r * 32 + lane;
+        start_state[r] = a < A.k ? T.enc(A.slot_state[a]) : dead;
+        if (r * 32 < static_cast<int>(A.k)) start_live |= 1u << r;
+    }
+
+    for (uint64_t task = warp0; task < n_tasks; task += n_warps) {
+        const uint64_t chunk0 = task * 64;
+        uint64_t pos[2] = {0, 0}, end[2] = {0, 0};
+        uint32_t s[2] = {dead, dead};
+        uint32_t alive[2][R];
+        bool pend[2] = {false, false};
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) alive[nb][r] = 0;
+            for (uint32_t j = 0; j < 32; ++j) {
+                const uint64_t ch = chunk0 + nb * 32 + j;
+                if (ch >= p.c) break;
+                uint64_t cp;
+                uint32_t cs;
+                uint32_t al[R];
+                if (speculate_chunk<R, LUT>(p, T, ch, lane, start_state, start_live, dead, &cp, &cs, al)) {
+                    if (lane == j) {
+                        pos[nb] = cp;
+                        s[nb] = cs;
+                        pend[nb] = true;
+#pragma unroll
+                        for (int r = 0; r < R; ++r) alive[nb][r] = al[r];
+                    }
+                }
+            }
+        }
+        // ---------------- converged phase: two chains per lane over shared windows
+        uint64_t wb[2];
+        uint32_t nwin[2];
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb) {
+            if (pend[nb]) end[nb] = chunk_begin(chunk0 + nb * 32 + lane + 1, p.len, p.c);
+            const uint64_t stop = min(end[nb], lim);
+            wb[nb] = pos[nb] & ~static_cast<uint64_t>(15);
+            nwin[nb] = (pend[nb] && wb[nb] < stop)
+                           ? static_cast<uint32_t>((stop - wb[nb] + kC2Win - 1) / kC2Win) : 0;
+        }
+        const uint32_t max_win = __reduce_max_sync(kFull, max(nwin[0], nwin[1]));
+        if (max_win) {
+            const uint32_t g = lane & 1;
+            uint4 v[4];
+            // instruction u loads window j = 16u + (lane >> 1) (chunk chunk0 + j), granule g
+            auto fetch = [&](uint32_t r) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int src = (16 * u + (lane >> 1)) & 31;
+                    const int nb = u >> 1;
+                    const uint64_t a = __shfl_sync(kFull, wb[nb], src) + static_cast<uint64_t>(kC2Win) * r + 16 * g;
+                    const uint32_t nw = __shfl_sync(kFull, nwin[nb], src);
+                    v[u] = (r < nw && a + 16 <= lim) ? __ldg(reinterpret_cast<const uint4 *>(p.text + a))
+                                                     : make_uint4(0, 0, 0, 0);
+                }
+            };
+            auto stash = [&]() {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t j = 16 * u + (lane >> 1);
+                    const uint32_t addr = stg + j * kC2Stride + 16 * g;
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
+                                 ::"r"(addr), "r"(v[u].x), "r"(v[u].y), "r"(v[u].z), "r"(v[u].w) : "memory");
+                }
+            };
+            fetch(0);
+            stash();
+            __syncwarp();
+            const uint32_t sb0 = stg + lane * kC2Stride, sb1 = stg + (32 + lane) * kC2Stride;
+            for (uint32_t r = 0; r < max_win; ++r) {
+                if (r + 1 < max_win) fetch(r + 1);
+                bool full[2], have[2];
+                uint64_t lo[2], hi[2], ws[2];
+#pragma unroll
+                for (int nb = 0; nb < 2; ++nb) {
+                    ws[nb] = wb[nb] + static_cast<uint64_t>(kC2Win) * r;
+                    have[nb] = r < nwin[nb] && s[nb] != dead;
+                    const uint64_t stop = min(end[nb], lim);
+                    lo[nb] = max(pos[nb], ws[nb]);
+                    hi[nb] = min(stop, ws[nb] + kC2Win);
+                    full[nb] = have[nb] && lo[nb] == ws[nb] && hi[nb] == ws[nb] + kC2Win;
+                }
+                if (full[0] && full[1]) {
+                    run_granule2(T, s[0], sb0, s[1], sb1);
+                    run_granule2(T, s[0], sb0 + 16, s[1], sb1 + 16);
+                } else {
+#pragma unroll
+                    for (int nb = 0; nb < 2; ++nb) {
+                        if (!have[nb]) continue;
+                        const uint32_t sb = nb ? sb1 : sb0;
+                        if (full[nb]) {
+                            s[nb] = run_granule(T, s[nb], sb);
+                            s[nb] = run_granule(T, s[nb], sb + 16);
+                        } else {
+                            for (uint64_t q = lo[nb]; q < hi[nb]; ++q)
+                                s[nb] = T.next(s[nb], T.cls_of(lds_u8(sb + static_cast<uint32_t>(q - ws[nb]))));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int nb = 0; nb < 2; ++nb)
+                    if (have[nb]) pos[nb] = hi[nb];
+                __syncwarp();
+                if (r + 1 < max_win) {
+                    stash();
+                    __syncwarp();
+                }
+            }
+        }
+        // tails past the last 16-byte boundary of the text, then rows and summaries
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb) {
+            if (!pend[nb]) continue;
+            while (pos[nb] < end[nb] && s[nb] != dead) {
+                s[nb] = T.next(s[nb], T.cls_of(__ldg(p.text + pos[nb])));
+                ++pos[nb];
+            }
+            const uint64_t ch = chunk0 + nb * 32 + lane;
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r) any |= alive[nb][r] != 0;
+            const uint32_t sid = T.id(s[nb]);
+            const uint16_t val = s[nb] == dead ? kUndef : static_cast<uint16_t>(sid);
+            write_row<R>(p.maps + ch * A.k, A.k, alive[nb], val);
+            p.dinfo[ch] = (any && s[nb] != dead) ? ((1u << 16) | sid) : static_cast<uint32_t>(kUndef);
         }
     }
 }
@@ -688,42 +1204,141 @@ int smem_optin_limit() {
 
 enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3 };
 
+// How one reach launch is laid out: table layout, text path, block/grid, shared memory.
+struct ReachPlan {
+    uint32_t mode = kModePlain;
+    int R = 1;
+    int tis = 0;                 // compact table in shared memory (Plain only)
+    int path = kPathGlobal;      // how the converged phase reads the text
+    int block = 256;
+    int grid = 1;
+    size_t smem = 0;
+    uint32_t staging_offset = 0;
+};
+
 template <int R>
 constexpr int block_cap() { return R <= 4 ? 1024 : 512; }
 
 // Launch (or, with per_sm != nullptr, size) one instantiation of the reach kernel.
-template <int R, class LUT>
-cudaError_t reach_one(const ReachArgs &a, int table_in_smem, int grid, int block, size_t smem,
-                      cudaStream_t st, int *per_sm) {
-    auto kern = rid_reach_kernel<R, LUT, block_cap<R>()>;
-    if (smem > 48 * 1024) {
+template <int R>
+constexpr int block_cap2() { return R <= 4 ? 768 : 512; }
+
+template <int R, class LUT, int PATH>
+cudaError_t reach_one(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
+    using KernT = void (*)(ReachArgs, int, uint32_t);
+    KernT kern = PATH == kPathCoop2 ? rid_reach2_kernel<R, LUT, block_cap2<R>()>
+                                    : rid_reach_kernel<R, LUT, block_cap<R>(), PATH == kPathCoop2 ? kPathGlobal : PATH>;
+    if (pl.smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+                                             static_cast<int>(pl.smem));
         if (e != cudaSuccess) return e;
     }
-    if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, block, smem);
-    kern<<<grid, block, smem, st>>>(a, table_in_smem);
+    if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, pl.block, pl.smem);
+    kern<<<pl.grid, pl.block, pl.smem, st>>>(a, pl.tis, pl.staging_offset);
     return cudaGetLastError();
 }
 
-template <class LUT>
-cudaError_t reach_r(int R, const ReachArgs &a, int tis, int grid, int block, size_t smem,
-                    cudaStream_t st, int *per_sm) {
-    switch (R) {
-        case 1: return reach_one<1, LUT>(a, tis, grid, block, smem, st, per_sm);
-        case 2: return reach_one<2, LUT>(a, tis, grid, block, smem, st, per_sm);
-        case 4: return reach_one<4, LUT>(a, tis, grid, block, smem, st, per_sm);
-        default: return reach_one<8, LUT>(a, tis, grid, block, smem, st, per_sm);
+template <class LUT, int PATH>
+cudaError_t reach_r(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
+    switch (pl.R) {
+        case 1: return reach_one<1, LUT, PATH>(a, pl, st, per_sm);
+        case 2: return reach_one<2, LUT, PATH>(a, pl, st, per_sm);
+        case 4: return reach_one<4, LUT, PATH>(a, pl, st, per_sm);
+        default: return reach_one<8, LUT, PATH>(a, pl, st, per_sm);
     }
 }
 
-cudaError_t reach_dispatch(uint32_t mode, int R, const ReachArgs &a, int tis, int grid, int block,
-                           size_t smem, cudaStream_t st, int *per_sm) {
-    switch (mode) {
-        case kModeRep16: return reach_r<LutRep<true>>(R, a, tis, grid, block, smem, st, per_sm);
-        case kModeRep32: return reach_r<LutRep<false>>(R, a, tis, grid, block, smem, st, per_sm);
-        default: return reach_r<LutPlain>(R, a, tis, grid, block, smem, st, per_sm);
+template <int PATH>
+cudaError_t reach_m(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
+    switch (pl.mode) {
+        case kModeRep16: return reach_r<LutRep<true>, PATH>(a, pl, st, per_sm);
+        case kModeRep32: return reach_r<LutRep<false>, PATH>(a, pl, st, per_sm);
+        default: return reach_r<LutPlain, PATH>(a, pl, st, per_sm);
     }
+}
+
+cudaError_t reach_dispatch(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
+    switch (pl.path) {
+        case kPathBulk: return reach_m<kPathBulk>(a, pl, st, per_sm);
+        case kPathCoop: return reach_m<kPathCoop>(a, pl, st, per_sm);
+        case kPathCoop2: return reach_m<kPathCoop2>(a, pl, st, per_sm);
+        default: return reach_m<kPathGlobal>(a, pl, st, per_sm);
+    }
+}
+
+// Choose the layout of a reach launch.  Defaults: the smallest lane-replicated table that fits
+// (16-bit, then 32-bit offsets), else the compact table; text staged by bulk copies when the
+// text is 16-byte aligned and the staging ring fits next to the table; one block per SM with
+// as many warps as fit; a grid of one wave.
+int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *text,
+               const ReachArgs &ra, int sms, ReachPlan *out) {
+    ReachPlan pl;
+    pl.R = A.k <= 32 ? 1 : A.k <= 64 ? 2 : A.k <= 128 ? 4 : 8;
+    const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024;
+    uint32_t mode = tuning ? tuning->table_mode : 0;
+    const size_t rep16 = LutRep<true>::smem_bytes(A), rep32 = LutRep<false>::smem_bytes(A);
+    const bool ok16 = LutRep<true>::fits16(A) && rep16 <= limit, ok32 = rep32 <= limit;
+    if (mode == 0) mode = ok16 ? kModeRep16 : ok32 ? kModeRep32 : kModePlain;
+    if ((mode == kModeRep16 && !ok16) || (mode == kModeRep32 && !ok32)) return RIDFA_E_ARG;
+    if (mode < kModePlain || mode > kModeRep32) return RIDFA_E_ARG;
+    pl.mode = mode;
+    const size_t plain_bytes = LutPlain::smem_bytes(A);
+    pl.tis = (mode == kModePlain && plain_bytes <= limit) ? 1 : 0;
+    const size_t table_smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : (pl.tis ? plain_bytes : 256);
+    const int cap = pl.R <= 4 ? 1024 : 512;
+    const uint32_t text_path = tuning ? tuning->text_path : 0;
+    if (text_path > 4) return RIDFA_E_ARG;
+    pl.staging_offset = static_cast<uint32_t>((table_smem + 127) & ~static_cast<size_t>(127));
+    const size_t room = limit > pl.staging_offset ? limit - pl.staging_offset : 0;
+    const bool aligned = (reinterpret_cast<uintptr_t>(text) & 15) == 0;
+    int block = (tuning && tuning->block_threads) ? static_cast<int>(tuning->block_threads) : 0;
+    auto fits = [&](uint32_t per_warp) {
+        const int w = static_cast<int>(std::min<size_t>(cap / 32, room / per_warp));
+        return (block == 0 ? w >= 4 : block / 32 <= w) ? w : 0;
+    };
+    const int cap2 = pl.R <= 4 ? 768 : 512;
+    auto fits2 = [&](uint32_t per_warp) {
+        const int w = static_cast<int>(std::min<size_t>(cap2 / 32, room / per_warp));
+        return (block == 0 ? w >= 4 : block / 32 <= w) ? w : 0;
+    };
+    const int w_coop = fits(kWarpCoopBytes), w_bulk = fits(kWarpStageBytes), w_coop2 = fits2(kWarpCoop2Bytes);
+    // auto: one chain per lane with cooperative staging (16-byte-aligned text, buffers fit),
+    // else plain global loads.  (Two chains per lane and bulk copies measured slower on GB300.)
+    if (text_path == 0)
+        pl.path = !aligned ? kPathGlobal : w_coop ? kPathCoop : kPathGlobal;
+    else if (text_path == 1) pl.path = kPathGlobal;
+    else if (text_path == 2) pl.path = kPathBulk;
+    else if (text_path == 3) pl.path = kPathCoop;
+    else pl.path = kPathCoop2;
+    if (pl.path == kPathBulk && !(aligned && w_bulk)) return RIDFA_E_ARG;
+    if (pl.path == kPathCoop && !(aligned && w_coop)) return RIDFA_E_ARG;
+    if (pl.path == kPathCoop2 && !(aligned && w_coop2)) return RIDFA_E_ARG;
+    const int warps_fit = pl.path == kPathBulk    ? w_bulk
+                          : pl.path == kPathCoop  ? w_coop
+                          : pl.path == kPathCoop2 ? w_coop2
+                                                  : cap / 32;
+    if (block == 0) block = pl.path == kPathGlobal ? (mode == kModePlain ? 256 : cap) : warps_fit * 32;
+    if (block < 32 || block > (pl.path == kPathCoop2 ? cap2 : cap) || block % 32) return RIDFA_E_ARG;
+    pl.block = block;
+    pl.smem = pl.path == kPathBulk    ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpStageBytes
+              : pl.path == kPathCoop  ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpCoopBytes
+              : pl.path == kPathCoop2 ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpCoop2Bytes
+                                      : table_smem;
+    const uint64_t tasks = (static_cast<uint64_t>(ra.c) + (pl.path == kPathCoop2 ? 63 : 31)) /
+                           (pl.path == kPathCoop2 ? 64 : 32);
+    if (tuning && tuning->grid_blocks) {
+        pl.grid = static_cast<int>(tuning->grid_blocks);
+    } else {
+        int per_sm = 0;
+        cudaError_t e = reach_dispatch(ra, pl, nullptr, &per_sm);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (per_sm < 1) return RIDFA_E_UNSUPPORTED;
+        const uint64_t wpb = block / 32;
+        const uint64_t need = (tasks + wpb - 1) / wpb;
+        pl.grid = static_cast<int>(std::min<uint64_t>(need, static_cast<uint64_t>(sms) * per_sm));
+    }
+    *out = pl;
+    return RIDFA_OK;
 }
 
 int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, size_t len,
@@ -787,37 +1402,9 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     // ---- reach
     ReachArgs ra{A, d_text, len, n_chunks, maps, dinfo, status, 8};
     if (tuning && tuning->probe_interval) ra.probe = tuning->probe_interval;
-    const int R = H.k <= 32 ? 1 : H.k <= 64 ? 2 : H.k <= 128 ? 4 : 8;
-    const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024;
-    // table layout: lane-replicated 16-bit offsets, else 32-bit offsets, else the compact table
-    uint32_t mode = tuning ? tuning->table_mode : 0;
-    const size_t rep16 = LutRep<true>::smem_bytes(A), rep32 = LutRep<false>::smem_bytes(A);
-    if (mode == 0)
-        mode = (LutRep<true>::fits16(A) && rep16 <= limit) ? kModeRep16
-               : (rep32 <= limit) ? kModeRep32 : kModePlain;
-    if (mode == kModeRep16 && !(LutRep<true>::fits16(A) && rep16 <= limit)) return RIDFA_E_ARG;
-    if (mode == kModeRep32 && rep32 > limit) return RIDFA_E_ARG;
-    if (mode < kModePlain || mode > kModeRep32) return RIDFA_E_ARG;
-    const size_t plain_bytes = LutPlain::smem_bytes(A);
-    const int tis = (mode == kModePlain && plain_bytes <= limit) ? 1 : 0;
-    const size_t smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : (tis ? plain_bytes : 256);
-    const int cap = R <= 4 ? 1024 : 512;
-    int block = (tuning && tuning->block_threads) ? static_cast<int>(tuning->block_threads)
-                                                  : (mode == kModePlain ? 256 : cap);
-    if (block < 32 || block > cap || block % 32) return RIDFA_E_ARG;
-    const uint64_t tasks = (c + 31) / 32;
-    int grid;
-    if (tuning && tuning->grid_blocks) {
-        grid = static_cast<int>(tuning->grid_blocks);
-    } else {
-        int per_sm = 0;
-        e = reach_dispatch(mode, R, ra, tis, 0, block, smem, st, &per_sm);
-        if (e != cudaSuccess) return cuda_fail(e);
-        if (per_sm < 1) return RIDFA_E_UNSUPPORTED;
-        const uint64_t warps_per_block = block / 32;
-        const uint64_t need = (tasks + warps_per_block - 1) / warps_per_block;
-        grid = static_cast<int>(std::min<uint64_t>(need, static_cast<uint64_t>(sms) * per_sm));
-    }
+    ReachPlan plan;
+    err = plan_reach(A, tuning, d_text, ra, sms, &plan);
+    if (err != RIDFA_OK) return err;
     const bool prof = tuning && tuning->profile;
     if (prof) {
         for (auto &ev : S->ev)
@@ -829,7 +1416,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
             }
         cudaEventRecord(static_cast<cudaEvent_t>(S->ev[0]), st);
     }
-    e = reach_dispatch(mode, R, ra, tis, grid, block, smem, st, nullptr);
+    e = reach_dispatch(ra, plan, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
     if (prof) cudaEventRecord(static_cast<cudaEvent_t>(S->ev[1]), st);
 
@@ -849,6 +1436,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e);
         *h_accept = *S->h_accept_pinned;
+        if (*S->h_status_pinned & kStatusTimeout) return RIDFA_E_TIMEOUT;
         if (*S->h_status_pinned & kStatusBad) return RIDFA_E_STATE;
     }
     return RIDFA_OK;
@@ -897,23 +1485,10 @@ int launch_with_buffers(const HostAutomaton &H, const PreparedBuffers &B, const 
     Automaton A{B.trans, B.classmap, B.final_bits, B.ifmask, B.slot_state,
                 H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
     ReachArgs ra{A, d_text, len, n_chunks, B.maps, B.dinfo, B.status, 8};
-    const int R = H.k <= 32 ? 1 : H.k <= 64 ? 2 : H.k <= 128 ? 4 : 8;
-    const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024;
-    const size_t rep16 = LutRep<true>::smem_bytes(A), rep32 = LutRep<false>::smem_bytes(A);
-    const uint32_t mode = (LutRep<true>::fits16(A) && rep16 <= limit) ? kModeRep16
-                          : (rep32 <= limit) ? kModeRep32 : kModePlain;
-    const size_t plain_bytes = LutPlain::smem_bytes(A);
-    const int tis = (mode == kModePlain && plain_bytes <= limit) ? 1 : 0;
-    const size_t smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : (tis ? plain_bytes : 256);
-    const int block = mode == kModePlain ? 256 : (R <= 4 ? 1024 : 512);
-    int per_sm = 0;
-    e = reach_dispatch(mode, R, ra, tis, 0, block, smem, st, &per_sm);
-    if (e != cudaSuccess) return cuda_fail(e);
-    if (per_sm < 1) return RIDFA_E_UNSUPPORTED;
-    const uint64_t tasks = (c + 31) / 32;
-    const uint64_t need = (tasks + block / 32 - 1) / (block / 32);
-    const int grid = static_cast<int>(std::min<uint64_t>(need, static_cast<uint64_t>(sms) * per_sm));
-    e = reach_dispatch(mode, R, ra, tis, grid, block, smem, st, nullptr);
+    ReachPlan plan;
+    int err = plan_reach(A, nullptr, d_text, ra, sms, &plan);
+    if (err != RIDFA_OK) return err;
+    e = reach_dispatch(ra, plan, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
     JoinArgs ja{A, n_chunks, B.maps, B.dinfo, B.status, B.partials, B.ticket, B.accept,
                 static_cast<uint32_t>(per_thread)};
@@ -968,6 +1543,7 @@ extern "C" int ridfa_last_status(const ridfa_program *prog, void *stream) {
         cudaError_t e = cudaMemcpyAsync(s.h_status_pinned, status, 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return ridfa::cuda_fail(e);
+        if (*s.h_status_pinned & 4u) return RIDFA_E_TIMEOUT;
         return (*s.h_status_pinned & 2u) ? RIDFA_E_STATE : RIDFA_OK;
     }
     return RIDFA_OK;

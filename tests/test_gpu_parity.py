@@ -153,6 +153,33 @@ def test_many_distinct_end_states(nb):
     check(re_src, y, 100, dfa_too=False)
 
 
+@pytest.mark.parametrize("path", [1, 2, 3, 4])
+def test_text_paths_agree(path):
+    """16-byte global loads and bulk-copy staging give the same maps, on aligned texts and on
+    texts that start 1..15 bytes past an alignment boundary (bulk copies then refuse)."""
+    x = textgen.c3_text(300_000, seed=81)
+    for c in (1, 31, 1000, 9000):
+        check(textgen.C3_RE, x, c, tuning=dict(text_path=path), dfa_too=(c == 1000))
+    prog = lib.ridfa_compile(textgen.C3_RE)
+    o, ser = oracle(textgen.C3_RE)
+    base = torch.from_numpy(np.concatenate([np.zeros(16, np.uint8), x])).to("cuda:0")
+    for off in (1, 3, 8, 15):
+        y = x[off:]
+        d = base[16 + off:]
+        if path in (2, 3, 4):
+            with pytest.raises(lib.RidfaError) as e:
+                lib.ridfa_recognize(prog, d, y.size, 100, tuning=dict(text_path=path))
+            assert e.value.code == -1
+            continue
+        maps = torch.empty((100, prog.info["k"]), dtype=torch.int16, device="cuda:0")
+        acc = lib.ridfa_recognize(prog, d, y.size, 100, tuning=dict(text_path=path), d_chunk_maps=maps)
+        assert acc == ser.accepts(y)
+        got = maps.cpu().numpy().view(np.uint16)
+        want = o.lambda_rows(y, 100, [0, 1, 50, 98, 99])
+        for i in want:
+            assert np.array_equal(got[i], want[i])
+
+
 @pytest.mark.parametrize("mode", [1, 2, 3])
 def test_tuning_variants_agree(mode):
     """Every table layout (compact, lane-replicated 16/32-bit) and launch shape gives the same
@@ -160,7 +187,10 @@ def test_tuning_variants_agree(mode):
     x = textgen.c3_text(1 << 18, seed=77)
     for t in [dict(probe_interval=1), dict(probe_interval=64), dict(block_threads=64),
               dict(grid_blocks=1), dict(block_threads=128, grid_blocks=3),
-              dict(block_threads=1024), dict()]:
+              dict(block_threads=1024), dict(), dict(text_path=2, block_threads=128),
+              dict(text_path=2, grid_blocks=2), dict(text_path=1, block_threads=1024),
+              dict(text_path=3, block_threads=96), dict(text_path=3, grid_blocks=1),
+              dict(text_path=4, block_threads=64), dict(text_path=4, grid_blocks=1), dict(text_path=4)]:
         t["table_mode"] = mode
         check(textgen.C3_RE, x, 1000, dfa_too=True, tuning=t)
     y = textgen.c1_text(1 << 16, seed=78)
