@@ -185,13 +185,143 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def build_batch_workload(lib, torch, dev, n_texts, seed):
+    """The batched configuration: n_texts texts (lognormal lengths) over 16 REs, resident in one
+    16-byte-aligned device buffer.  Returns (progs, items, total_bytes, device buffer, REs)."""
+    import numpy as np
+
+    import textgen.batch as tb
+    res = tb.standard_res()
+    kept = []
+    for r, body, alpha in tb.random_re_candidates(seed, 400):
+        try:
+            p = lib.ridfa_compile(r, build_dfa=False)
+        except lib.RidfaError:
+            continue
+        if 10 <= p.info["n_states"] <= 5000 and p.info["k"] <= lib.RIDFA_MAX_SLOTS:
+            kept.append((r, body, alpha))
+        if len(kept) == 13:
+            break
+    res = res + kept
+    progs = [lib.ridfa_compile(r, build_dfa=False) for r, _, _ in res]
+    texts, rid = [], []
+    for j, r, x, _ in tb.batch_texts(res, n_texts, seed + 1):
+        texts.append(x)
+        rid.append(r)
+    offs = np.zeros(len(texts), dtype=np.int64)
+    pos = 0
+    for i, x in enumerate(texts):
+        offs[i] = pos
+        pos = (pos + x.size + 15) & ~15
+    host = torch.empty(pos, dtype=torch.uint8, pin_memory=True)
+    hv = host.numpy()
+    for o, x in zip(offs, texts):
+        hv[o:o + x.size] = x
+    d = host.to(dev)
+    base = d.data_ptr()
+    items = [(base + int(o), int(x.size), r, 0) for o, x, r in zip(offs, texts, rid)]
+    total = int(sum(x.size for x in texts))
+    return progs, items, total, d, [r for r, _, _ in res], texts
+
+
+def run_batch(args, lib, torch, dev, stream, world, rank):
+    import numpy as np
+    t0 = time.perf_counter()
+    progs, items, total, d, res, texts = build_batch_workload(lib, torch, dev, args.batch_texts, args.seed)
+    gen_s = time.perf_counter() - t0
+    acc = torch.zeros(len(items), dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    b = lib.ridfa_batch_create(progs, items, acc, chunk_len=args.batch_chunk_len)
+    create_s = time.perf_counter() - t0
+    st = lib.ridfa_batch_get_stats(b)
+    for _ in range(args.warmup):
+        lib.ridfa_batch_run(b, stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            lib.ridfa_batch_run(b, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * total * args.steps / (ms / 1e3) / 1e9
+    got = acc.cpu().numpy().astype(bool)
+    # the plain one-text-per-launch path on the same texts (same chunk length), for comparison
+    L = st["chunk_len"]
+    acc1 = torch.zeros(1, dtype=torch.uint8, device=dev)
+    def one_pass():
+        for (ptr, n, r, _) in items:
+            lib.ridfa_recognize_async(progs[r], ptr, n, max(1, min(n, (n + L - 1) // L)), acc1, stream=stream)
+    one_pass()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    one_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_value = total / (e0.elapsed_time(e1) / 1e3) / 1e9
+    # spot check against the single-text path
+    rng = np.random.Generator(np.random.PCG64(5))
+    sample = rng.choice(len(items), size=min(64, len(items)), replace=False)
+    mism = 0
+    for i in sample:
+        ptr, n, r, _ = items[i]
+        mism += int(lib.ridfa_recognize(progs[r], ptr, n, max(1, min(n, 64)), stream=stream) != got[i])
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle.recognizer import SerialRecognizer
+        t0 = time.perf_counter()
+        nb = 0
+        sers = {}
+        for i in range(len(items)):
+            r = items[i][2]
+            if r not in sers:
+                sers[r] = SerialRecognizer(res[r])
+            sers[r].accepts(texts[i])
+            nb += texts[i].size
+            if time.perf_counter() - t0 > 12:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(nb / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first {nb} bytes of the batch, item by item, Thompson state-set simulation"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic",
+                "config": {"workload": f"batched: {len(items)} texts, lognormal median 256 KiB sigma 1, "
+                                       f"16 REs (3 single-text + 13 random), half mutated, one CUDA graph",
+                           "total_bytes": total, "chunk_len": L, "chunks": st["total_chunks"],
+                           "launches_in_graph": st["n_launches"], "tasks": st["n_tasks"],
+                           "join_segments": st["n_segments"], "graph": bool(st["graph"]),
+                           "accepted": int(got.sum()), "spot_check_mismatches": mism,
+                           "generate_s": round(gen_s, 1), "create_s": round(create_s, 2),
+                           "l2": "inputs larger than L2, no flush"},
+                "single_text_per_launch_GBps": round(single_value, 3),
+                "batched_over_single": round(value / single_value, 3),
+                "clocks": clk.summary(), "cpu_baseline": cpu,
+                "gpu_launches": args.steps * st["n_launches"]}
+        print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--batch-texts", type=int, default=10000)
+    ap.add_argument("--batch-chunk-len", type=int, default=0, help="0 = autotune")
     ap.add_argument("--text-bytes", type=int, default=None)
     ap.add_argument("--chunks", type=int, default=None)
     ap.add_argument("--seed", type=int, default=0x5EED02)
@@ -223,6 +353,12 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device(dev))
 
     name = args.workload
+    stream = torch.cuda.current_stream()
+    if name == "batch":
+        run_batch(args, lib, torch, dev, stream, world, rank)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     desc, n_default, c_default = WORKLOADS[name]
     n_req = args.text_bytes or n_default
     c = args.chunks or c_default

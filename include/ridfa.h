@@ -198,6 +198,62 @@ int ridfa_last_status(const ridfa_program *prog, void *stream);
  * events.  Errors: E_ARG (no profiled call yet), E_CUDA. */
 int ridfa_last_timings(const ridfa_program *prog, float *reach_ms, float *join_ms);
 
+/* ---- Batched recognition (the paper recognises one text at a time; a batch runs the same
+ * reach and join, exactly, for many (text, program) items at once).
+ * All items' chunks run in one persistent reach launch per shared-memory table layout (CTAs take
+ * tasks of up to 32 chunks per warp of one program from an atomic ticket and reload their tables
+ * only when the program changes) followed by one join launch over all texts; create() captures
+ * these launches into a CUDA graph that run() replays. */
+typedef struct {
+    const uint8_t *d_text;   /* device pointer (16-byte alignment of every text enables the
+                                cooperative staged text path; otherwise global loads are used) */
+    uint64_t len;            /* bytes; 0 allowed (accept = empty word in L) */
+    uint32_t prog;           /* index into progs[] */
+    uint32_t n_chunks;       /* 0: ceil(len / chunk_len); else 1 <= n_chunks <= len */
+} ridfa_batch_item;
+
+typedef struct {
+    uint32_t chunk_len;      /* bytes per chunk for items with n_chunks == 0; 0 = autotune: the
+                                length is looked up in a cache keyed by every program's
+                                (log2 |P|, log2 k, log2 C), else candidate lengths are timed on
+                                this batch and the winner is cached under those keys */
+    uint32_t no_graph;       /* 1: run() enqueues the launches directly instead of a CUDA graph */
+    uint32_t reserved[2];
+} ridfa_batch_opts;
+
+typedef struct {
+    uint64_t total_bytes;
+    uint64_t total_chunks;
+    uint32_t n_programs, n_launches, n_tasks, n_segments;
+    uint32_t chunk_len;      /* the chunk length in use */
+    uint32_t graph;          /* 1 if run() launches a CUDA graph */
+    uint64_t device_bytes;   /* device memory the batch holds (descriptors, maps, summaries) */
+} ridfa_batch_stats;
+
+typedef struct ridfa_batch ridfa_batch;
+
+/* Plan a batch: per-program device tables (uploaded if needed), chunking, tasks, join segments,
+ * device scratch (one allocation), and the CUDA graph.  The texts and d_accept (n_items bytes,
+ * device; d_accept[i] receives item i's accept bit) must stay valid while the batch is used; the
+ * programs must outlive it.  Errors: E_ARG, E_CHUNKS, E_UNSUPPORTED, E_NOMEM, E_CUDA. */
+int ridfa_batch_create(const ridfa_program *const *progs, uint32_t n_progs,
+                       const ridfa_batch_item *items, uint32_t n_items, uint8_t *d_accept,
+                       const ridfa_batch_opts *opts, ridfa_batch **out);
+
+/* Enqueue the whole batch on `stream` (one graph launch); asynchronous.  Runs of one batch must
+ * not overlap.  Errors: E_ARG, E_CUDA. */
+int ridfa_batch_run(ridfa_batch *batch, void *stream);
+
+int ridfa_batch_get_stats(const ridfa_batch *batch, ridfa_batch_stats *out);
+
+/* Synchronise the batch's device and release it.  NULL is a no-op. */
+void ridfa_batch_free(ridfa_batch *batch);
+
+/* One-shot: create (chunk length 8 KiB, no graph), run on `stream`, synchronise, free. */
+int ridfa_recognize_batch(const ridfa_program *const *progs, uint32_t n_progs,
+                          const ridfa_batch_item *items, uint32_t n_items, uint8_t *d_accept,
+                          void *stream);
+
 /* Roofline microbenchmarks (diagnostics; the paper has no counterpart).  Both allocate a 4-byte
  * sink and synchronise the current device.
  * ridfa_bench_smem_gather: the reach kernel's converged step alone -- per text byte one

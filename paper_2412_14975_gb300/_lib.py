@@ -279,3 +279,92 @@ def ridfa_bench_hbm_read(d_buf, nbytes):
     r, ms = _c.c_double(), _c.c_double()
     _check(_lib.ridfa_bench_hbm_read(_ptr(d_buf), int(nbytes), _c.byref(r), _c.byref(ms)), "ridfa_bench_hbm_read")
     return r.value
+
+
+# ---------------------------------------------------------------------------------- batches
+class BatchItem(_c.Structure):
+    _fields_ = [("d_text", _vp), ("len", _c.c_uint64), ("prog", _u32), ("n_chunks", _u32)]
+
+
+class BatchOpts(_c.Structure):
+    _fields_ = [("chunk_len", _u32), ("no_graph", _u32), ("reserved", _u32 * 2)]
+
+
+class BatchStats(_c.Structure):
+    _fields_ = [("total_bytes", _c.c_uint64), ("total_chunks", _c.c_uint64), ("n_programs", _u32),
+                ("n_launches", _u32), ("n_tasks", _u32), ("n_segments", _u32), ("chunk_len", _u32),
+                ("graph", _u32), ("device_bytes", _c.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_decl("ridfa_batch_create", _c.c_int, [_c.POINTER(_vp), _u32, _c.POINTER(BatchItem), _u32, _vp,
+                                       _c.POINTER(BatchOpts), _c.POINTER(_vp)])
+_decl("ridfa_batch_run", _c.c_int, [_vp, _vp])
+_decl("ridfa_batch_get_stats", _c.c_int, [_vp, _c.POINTER(BatchStats)])
+_decl("ridfa_batch_free", None, [_vp])
+_decl("ridfa_recognize_batch", _c.c_int, [_c.POINTER(_vp), _u32, _c.POINTER(BatchItem), _u32, _vp, _vp])
+
+
+def _batch_arrays(progs, items):
+    parr = (_vp * len(progs))(*[p.handle for p in progs])
+    iarr = (BatchItem * len(items))()
+    for i, (text, length, prog, n_chunks) in enumerate(items):
+        iarr[i] = BatchItem(_ptr(text) if length else None, int(length), int(prog), int(n_chunks))
+    return parr, iarr
+
+
+class Batch:
+    """Owns one ridfa_batch*; keeps its programs alive."""
+
+    def __init__(self, handle, progs):
+        self.handle = handle
+        self.progs = list(progs)
+
+    def close(self):
+        if self.handle:
+            _lib.ridfa_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        if not self.handle:
+            raise ValueError("batch is closed")
+        return self.handle
+
+
+def ridfa_batch_create(progs, items, d_accept, chunk_len=0, no_graph=False):
+    """items: list of (device text, length, program index, n_chunks or 0)."""
+    parr, iarr = _batch_arrays(progs, items)
+    opts = BatchOpts(int(chunk_len), int(bool(no_graph)), (_u32 * 2)(0, 0))
+    h = _vp()
+    _check(_lib.ridfa_batch_create(parr, len(progs), iarr, len(items), _ptr(d_accept), _c.byref(opts),
+                                   _c.byref(h)), "ridfa_batch_create")
+    return Batch(h.value, progs)
+
+
+def ridfa_batch_run(batch, stream=None):
+    _check(_lib.ridfa_batch_run(batch, _stream(stream)), "ridfa_batch_run")
+
+
+def ridfa_batch_get_stats(batch):
+    st = BatchStats()
+    _check(_lib.ridfa_batch_get_stats(batch, _c.byref(st)), "ridfa_batch_get_stats")
+    return st.as_dict()
+
+
+def ridfa_batch_free(batch):
+    batch.close()
+
+
+def ridfa_recognize_batch(progs, items, d_accept, stream=None):
+    parr, iarr = _batch_arrays(progs, items)
+    _check(_lib.ridfa_recognize_batch(parr, len(progs), iarr, len(items), _ptr(d_accept), _stream(stream)),
+           "ridfa_recognize_batch")

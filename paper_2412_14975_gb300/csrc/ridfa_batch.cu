@@ -1,0 +1,911 @@
+// Batched recognition: many texts against many programs in one CUDA graph.
+//
+// The paper recognises one text at a time (Sec. 3.2).  A batch runs the same reach and join,
+// exactly, for every (text, program) item, with all items' chunks in one persistent reach launch
+// per table layout and one join launch, captured once into a CUDA graph and replayed by
+// ridfa_batch_run:
+//   * reach: CTAs take tasks (up to 32 chunks per warp of one program) from an atomic ticket;
+//     tasks are ordered by program, so a CTA reloads its shared-memory tables only when the
+//     program changes.  Each warp runs the speculative phase of its chunks (lanes = runs) and
+//     then finishes the converged runs one per lane, with the text staged by cp.async exactly as
+//     the single-text kernel does.  Chunk i of an item covers text[floor(i*len/c), ...).
+//   * join: one block per segment of up to 256 chunk boundaries of one text; each thread forms
+//     one transfer matrix M_i (as in the single-text join), the block multiplies them, and the
+//     last segment of a text (per-text atomic ticket) multiplies the segment products in order and
+//     evaluates lambda_1(q0) and the acceptance test.  A text with more than 32 distinct end
+//     states in some chunk is finished by that last block propagating if_min(PLAS_i) chunk by chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "ridfa_internal.h"
+#include "ridfa_kernels.cuh"
+
+namespace ridfa {
+namespace {
+
+struct TextDesc {             // one item
+    const uint8_t *text;
+    uint64_t len;
+    uint64_t chunk_base;      // first chunk of this text in its program's chunk numbering
+    uint32_t c;               // chunks (0 for an empty text)
+    uint32_t item;            // index into d_accept
+};
+
+struct ProgDesc {
+    Automaton A;
+    const TextDesc *texts;    // this program's texts, chunk_base ascending
+    uint16_t *maps;           // [n_chunks][k]
+    uint32_t *dinfo;          // [n_chunks]
+    uint32_t n_texts;
+    uint32_t tis;             // compact table in shared memory (Plain layout)
+    uint32_t text0;           // global index of texts[0]
+    uint32_t pad;
+};
+
+struct TaskDesc {
+    uint64_t chunk0;
+    uint32_t prog;
+    uint32_t count;
+};
+
+struct SegDesc {
+    uint64_t b0;              // first boundary (chunk index >= 1) of the segment
+    uint32_t prog, text;      // text: global text index
+    uint32_t count, seg, nseg, part0;
+};
+
+struct BatchReachArgs {
+    const ProgDesc *progs;
+    const TaskDesc *tasks;
+    uint32_t n_tasks;
+    uint32_t probe;
+    uint32_t *counter;
+    uint32_t *status;
+    RunEntry *runs;           // [grid warps][kRunsPerWarp]
+    uint32_t *finals;         // [grid warps][kFinalsPerWarp]
+};
+
+struct BatchJoinArgs {
+    const ProgDesc *progs;
+    const TextDesc *texts;    // all texts, grouped by program
+    const SegDesc *segs;
+    uint32_t *partials;       // [segments][kPartialWords]
+    uint32_t *tickets;        // [texts]
+    uint32_t *flags;          // [texts]
+    uint8_t *accept;
+    uint32_t *status;
+};
+
+constexpr int kBatchJoinThreads = 256;
+
+// Text of program-local chunk ch, starting the search at *t (chunks of a slice ascend).
+__device__ __forceinline__ const TextDesc *text_of(const ProgDesc &P, uint64_t ch, uint32_t *t) {
+    uint32_t i = *t;
+    while (i + 1 < P.n_texts && P.texts[i + 1].chunk_base <= ch) ++i;
+    *t = i;
+    return &P.texts[i];
+}
+
+__device__ __forceinline__ uint32_t first_text(const ProgDesc &P, uint64_t ch) {
+    uint32_t lo = 0, hi = P.n_texts - 1;          // last text with chunk_base <= ch
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (P.texts[mid].chunk_base <= ch) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int R, class LUT, int BLOCK, bool COOP>
+__global__ void __launch_bounds__(BLOCK, 1) rid_reach_batch_kernel(BatchReachArgs b, uint32_t staging_offset) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ uint32_t s_task;
+    LUT T;
+    int cur = -1;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t stg_base = smem_addr(smem) + staging_offset + warp * kWarpCoopBytes;
+    const uint64_t gwarp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    RunEntry *const wruns = b.runs + gwarp * kRunsPerWarp;
+    uint32_t *const wfin = b.finals + gwarp * kFinalsPerWarp;
+    uint32_t *const wball = wfin + kRunsPerWarp;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(b.counter, 1u);
+        __syncthreads();
+        const uint32_t t = s_task;
+        if (t >= b.n_tasks) break;
+        const TaskDesc task = b.tasks[t];
+        const ProgDesc &P = b.progs[task.prog];
+        const Automaton &A = P.A;
+        if (static_cast<int>(task.prog) != cur) {
+            T.setup(A, smem, P.tis != 0);
+            __syncthreads();
+            cur = static_cast<int>(task.prog);
+        }
+        const uint64_t c0 = task.chunk0 + 32ull * warp;
+        const uint64_t cend = task.chunk0 + task.count;
+        if (c0 < cend) {
+            const uint32_t nch = static_cast<uint32_t>(min(static_cast<uint64_t>(32), cend - c0));
+            // slot start states of this lane (slot a = r*32 + lane)
+            const uint32_t dead = T.enc(A.n);
+            uint32_t start_state[R];
+            uint32_t start_live = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t a = r * 32 + lane;
+                start_state[r] = a < A.k ? T.enc(__ldg(A.slot_state + a)) : dead;
+                if (r * 32 < static_cast<int>(A.k)) start_live |= 1u << r;
+            }
+            // ---- speculative phase, chunk by chunk; up to kMaxRun runs handed off per chunk
+            uint32_t my_hand = 0;     // owner lane j of a handed-off chunk: (m << 16) | first run
+            uint32_t my_ti = 0;       // owner lane j: text index of chunk j
+            uint32_t nruns = 0, handed = 0;
+            uint32_t amask[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) amask[r] = 0;
+            uint32_t ti = first_text(P, c0);
+            for (uint32_t j = 0; j < nch; ++j) {
+                const uint64_t ch = c0 + j;
+                const TextDesc *td = text_of(P, ch, &ti);
+                if (lane == j) my_ti = ti;
+                const uint64_t i = ch - td->chunk_base;
+                const uint64_t beg = chunk_begin(i, td->len, td->c), end = chunk_begin(i + 1, td->len, td->c);
+                uint64_t hp = 0;
+                uint32_t d, al[R];
+                const int m = speculate<R, LUT>(T, A, td->text, beg, end, b.probe, lane, start_state, start_live,
+                                                dead, P.maps + ch * A.k, P.dinfo + ch, b.status, true, false, &hp,
+                                                &d, al);
+                if (m >= 1) {
+                    handed |= 1u << j;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) amask[r] |= ((al[r] >> lane) & 1u) << j;
+                    if (lane < static_cast<uint32_t>(m))
+                        wruns[nruns + lane] = RunEntry{hp, d, static_cast<uint16_t>(j), static_cast<uint16_t>(lane)};
+                    if (lane == j) my_hand = (static_cast<uint32_t>(m) << 16) | nruns;
+                    nruns += static_cast<uint32_t>(m);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) wball[r * 32 + lane] = amask[r];
+            __syncwarp();
+            // ---- converged phase: each lane finishes one run (rounds of 32 runs)
+            uint32_t fin_reg = dead;
+            for (uint32_t rb = 0; rb < nruns; rb += 32) {
+                const uint32_t idx = rb + lane;
+                const bool pending = idx < nruns;
+                uint64_t pos = 0, end = 0, lim = 0;
+                uint32_t s = dead, jj = 0;
+                if (pending) {
+                    const RunEntry e = wruns[idx];
+                    pos = e.pos;
+                    s = e.state;
+                    jj = e.chunk;
+                }
+                const uint32_t tix = __shfl_sync(kFull, my_ti, jj);
+                const uint8_t *tx = nullptr;
+                if (pending) {
+                    const TextDesc &td = P.texts[tix];
+                    end = chunk_begin(c0 + jj - td.chunk_base + 1, td.len, td.c);
+                    lim = td.len & ~static_cast<uint64_t>(15);
+                    tx = td.text;
+                }
+                if (COOP && __any_sync(kFull, pending))
+                    coop_converge<LUT, false>(T, stg_base, lane, pending, tx, lim, min(end, lim), pos, s, dead);
+                if (pending) {
+                    tail_converge<LUT, !COOP>(T, tx, pos, end, s, dead);
+                    if (nruns > 32) wfin[idx] = s;
+                    else fin_reg = s;
+                }
+            }
+            __syncwarp();
+            // ---- rows of the handed-off chunks, one chunk at a time by the warp
+#pragma unroll
+            for (int r = 0; r < R; ++r) amask[r] = wball[r * 32 + lane];
+            for (uint32_t hm = handed; hm; hm &= hm - 1) {
+                const uint32_t j = __ffs(hm) - 1;
+                const uint32_t hand = __shfl_sync(kFull, my_hand, j);
+                const uint32_t m = hand >> 16, run0 = hand & 0xFFFF;
+                const uint32_t src = run0 + min(lane, m - 1);
+                uint32_t fin = __shfl_sync(kFull, fin_reg, src & 31);
+                if (nruns > 32) fin = wfin[src];
+                uint32_t am = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) am |= ((amask[r] >> j) & 1u) << r;
+                finish_handed_row<R, LUT>(T, P.maps + (c0 + j) * A.k, A.k, m, m >= 2, lane, am, fin, dead,
+                                          P.dinfo + c0 + j);
+            }
+        }
+        __syncthreads();   // every warp is done with this task before the tables may change
+    }
+}
+
+// ---------------------------------------------------------------------------- batch join
+struct BProd {
+    uint32_t nrows;           // 0xFFFFFFFF = identity
+    uint32_t rows[kMaxD];
+};
+
+__device__ void bcompose(BProd &a, const BProd &b) {
+    if (b.nrows == 0xFFFFFFFFu) return;
+    if (a.nrows == 0xFFFFFFFFu) {
+        a = b;
+        return;
+    }
+    for (uint32_t x = 0; x < a.nrows; ++x) {
+        uint32_t bits = a.rows[x], out = 0;
+        while (bits) {
+            const uint32_t z = __ffs(bits) - 1;
+            bits &= bits - 1;
+            out |= b.rows[z];
+        }
+        a.rows[x] = out;
+    }
+}
+
+// Distinct defined values of row i (ascending, at most kMaxD; 0xFFFFFFFF when wider).
+__device__ uint32_t bdistinct(const Automaton &A, const uint16_t *maps_t, const uint32_t *dinfo_t, uint64_t i,
+                              uint16_t *D) {
+    const uint32_t info = dinfo_t[i];
+    const uint32_t m = info >> 16;
+    if (m <= 1) {
+        D[0] = static_cast<uint16_t>(info & 0xFFFF);
+        return m;
+    }
+    if (m > kMaxD) return 0xFFFFFFFFu;
+    const uint16_t *row = maps_t + i * A.k;
+    uint32_t cnt = 0;
+    for (uint32_t a = 0; a < A.k; ++a) {
+        const uint16_t v = row[a];
+        if (v == kUndef) continue;
+        uint32_t j = 0;
+        while (j < cnt && D[j] < v) ++j;
+        if (j < cnt && D[j] == v) continue;
+        if (cnt == kMaxD) return 0xFFFFFFFFu;
+        for (uint32_t t = cnt; t > j; --t) D[t] = D[t - 1];
+        D[j] = v;
+        ++cnt;
+    }
+    return cnt;
+}
+
+__device__ __forceinline__ uint32_t bindex(const uint16_t *D, uint32_t m, uint16_t v) {
+    for (uint32_t j = 0; j < m; ++j)
+        if (D[j] == v) return j;
+    return 0xFFFFFFFFu;
+}
+
+__global__ void __launch_bounds__(kBatchJoinThreads) rid_join_batch_kernel(BatchJoinArgs J) {
+    __shared__ BProd s_prod[kBatchJoinThreads];
+    __shared__ bool s_last, s_wide;
+    __shared__ uint32_t s_vec[RIDFA_MAX_SLOTS / 32], s_nvec[RIDFA_MAX_SLOTS / 32];
+    __shared__ uint32_t s_acc;
+    __shared__ int s_wideflag, s_badflag;
+    if (threadIdx.x == 0) {
+        s_wideflag = 0;
+        s_badflag = 0;
+    }
+    __syncthreads();
+    const SegDesc seg = J.segs[blockIdx.x];
+    const ProgDesc &P = J.progs[seg.prog];
+    const Automaton &A = P.A;
+    const TextDesc &td = J.texts[seg.text];
+    const uint16_t *maps_t = P.maps + td.chunk_base * A.k;
+    const uint32_t *dinfo_t = P.dinfo + td.chunk_base;
+    const uint32_t tid = threadIdx.x;
+
+    BProd Pr;
+    Pr.nrows = 0xFFFFFFFFu;
+    bool wide = false, bad = false;
+    if (tid < seg.count) {
+        const uint64_t i = seg.b0 + tid;            // boundary between chunks i-1 and i
+        uint16_t Dp[kMaxD], Dc[kMaxD];
+        const uint32_t mp = bdistinct(A, maps_t, dinfo_t, i - 1, Dp);
+        const uint32_t mc = bdistinct(A, maps_t, dinfo_t, i, Dc);
+        if (mp == 0xFFFFFFFFu || mc == 0xFFFFFFFFu) {
+            wide = true;
+        } else {
+            Pr.nrows = mp;
+            const uint16_t *row = maps_t + i * A.k;
+            for (uint32_t x = 0; x < mp; ++x) {
+                const uint32_t *mask = A.ifmask + static_cast<uint64_t>(Dp[x]) * A.kw;
+                uint32_t out = 0;
+                for (uint32_t w = 0; w < A.kw; ++w) {
+                    uint32_t bits = mask[w];
+                    while (bits) {
+                        const uint32_t a = w * 32 + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const uint16_t v = row[a];
+                        if (v == kUndef) continue;
+                        const uint32_t y = bindex(Dc, mc, v);
+                        if (y == 0xFFFFFFFFu) bad = true;
+                        else out |= 1u << y;
+                    }
+                }
+                Pr.rows[x] = out;
+            }
+        }
+    }
+    if (bad) s_badflag = 1;
+    if (wide) s_wideflag = 1;
+    s_prod[tid] = Pr;
+    __syncthreads();
+    for (uint32_t stride = 1; stride < blockDim.x; stride *= 2) {
+        if ((tid % (2 * stride)) == 0 && tid + stride < blockDim.x) bcompose(s_prod[tid], s_prod[tid + stride]);
+        __syncthreads();
+    }
+    uint32_t *mine = J.partials + static_cast<uint64_t>(seg.part0 + seg.seg) * kPartialWords;
+    if (tid == 0) {
+        if (s_badflag) atomicOr(J.status, kStatusBad);
+        if (s_wideflag) atomicOr(&J.flags[seg.text], 1u);
+        mine[0] = s_prod[0].nrows;
+        if (s_prod[0].nrows != 0xFFFFFFFFu)
+            for (uint32_t x = 0; x < s_prod[0].nrows; ++x) mine[1 + x] = s_prod[0].rows[x];
+        __threadfence();
+        const uint32_t t = atomicAdd(&J.tickets[seg.text], 1u);
+        s_last = (t == seg.nseg - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid == 0) s_wide = (*reinterpret_cast<volatile uint32_t *>(&J.flags[seg.text]) & 1u) != 0;
+    __syncthreads();
+    const uint64_t c = td.c;
+    if (c == 0) {   // empty text: is the empty word in L?
+        if (tid == 0) J.accept[td.item] = is_final_state(A, A.slot_state[A.q0_slot]) ? 1 : 0;
+    } else if (s_wide) {
+        // sequential propagation of if_min(PLAS_i) over this text's chunks
+        const uint16_t v0 = maps_t[A.q0_slot];
+        if (c == 1 || v0 == kUndef) {
+            if (tid == 0) J.accept[td.item] = (v0 != kUndef && is_final_state(A, v0)) ? 1 : 0;
+        } else {
+            for (uint32_t w = tid; w < A.kw; w += blockDim.x) s_vec[w] = A.ifmask[static_cast<uint64_t>(v0) * A.kw + w];
+            __syncthreads();
+            for (uint64_t i = 1; i + 1 < c; ++i) {
+                for (uint32_t w = tid; w < A.kw; w += blockDim.x) s_nvec[w] = 0;
+                __syncthreads();
+                const uint16_t *row = maps_t + i * A.k;
+                for (uint32_t a = tid; a < A.k; a += blockDim.x) {
+                    if (!((s_vec[a >> 5] >> (a & 31)) & 1)) continue;
+                    const uint16_t v = row[a];
+                    if (v == kUndef) continue;
+                    for (uint32_t w = 0; w < A.kw; ++w) {
+                        const uint32_t m = A.ifmask[static_cast<uint64_t>(v) * A.kw + w];
+                        if (m) atomicOr(&s_nvec[w], m);
+                    }
+                }
+                __syncthreads();
+                for (uint32_t w = tid; w < A.kw; w += blockDim.x) s_vec[w] = s_nvec[w];
+                __syncthreads();
+            }
+            if (tid == 0) s_acc = 0;
+            __syncthreads();
+            const uint16_t *last = maps_t + (c - 1) * A.k;
+            for (uint32_t a = tid; a < A.k; a += blockDim.x)
+                if (((s_vec[a >> 5] >> (a & 31)) & 1) && last[a] != kUndef && is_final_state(A, last[a])) s_acc = 1;
+            __syncthreads();
+            if (tid == 0) J.accept[td.item] = s_acc ? 1 : 0;
+        }
+    } else if (tid == 0) {
+        BProd tot;
+        tot.nrows = 0xFFFFFFFFu;
+        for (uint32_t sgi = 0; sgi < seg.nseg; ++sgi) {
+            const volatile uint32_t *q = J.partials + static_cast<uint64_t>(seg.part0 + sgi) * kPartialWords;
+            BProd x;
+            x.nrows = q[0];
+            if (x.nrows != 0xFFFFFFFFu)
+                for (uint32_t r = 0; r < x.nrows; ++r) x.rows[r] = q[1 + r];
+            bcompose(tot, x);
+        }
+        const uint16_t v0 = maps_t[A.q0_slot];
+        uint8_t acc = 0;
+        if (v0 != kUndef) {
+            if (c == 1) {
+                acc = is_final_state(A, v0) ? 1 : 0;
+            } else {
+                uint16_t D0[kMaxD], Dl[kMaxD];
+                const uint32_t m0 = bdistinct(A, maps_t, dinfo_t, 0, D0);
+                const uint32_t x0 = bindex(D0, m0, v0);
+                const uint32_t ml = bdistinct(A, maps_t, dinfo_t, c - 1, Dl);
+                if (x0 == 0xFFFFFFFFu || tot.nrows == 0xFFFFFFFFu || ml == 0xFFFFFFFFu) {
+                    atomicOr(J.status, kStatusBad);
+                } else {
+                    const uint32_t bits = tot.rows[x0];
+                    for (uint32_t y = 0; y < ml; ++y)
+                        if (((bits >> y) & 1) && is_final_state(A, Dl[y])) acc = 1;
+                }
+            }
+        }
+        J.accept[td.item] = acc;
+    }
+    if (tid == 0) {   // ready for the next replay
+        J.tickets[seg.text] = 0;
+        J.flags[seg.text] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------- host side
+enum BMode : uint32_t { kBPlain = 1, kBRep16 = 2, kBRep32 = 3 };
+
+struct LaunchGroup {          // one persistent reach launch
+    uint32_t mode = kBPlain;
+    int R = 1;
+    bool coop = false;
+    std::vector<uint32_t> progs;   // batch program indices in this launch
+    uint32_t task0 = 0, n_tasks = 0;
+    size_t table_smem = 0;
+};
+
+template <int R, class LUT, bool COOP>
+cudaError_t batch_reach_one(const BatchReachArgs &a, int grid, int block, size_t smem, uint32_t stg,
+                            cudaStream_t st, int *per_sm) {
+    auto kern = rid_reach_batch_kernel<R, LUT, (R <= 4 ? 1024 : 512), COOP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, block, smem);
+    kern<<<grid, block, smem, st>>>(a, stg);
+    return cudaGetLastError();
+}
+
+template <class LUT, bool COOP>
+cudaError_t batch_reach_r(int R, const BatchReachArgs &a, int grid, int block, size_t smem, uint32_t stg,
+                          cudaStream_t st, int *per_sm) {
+    switch (R) {
+        case 1: return batch_reach_one<1, LUT, COOP>(a, grid, block, smem, stg, st, per_sm);
+        case 2: return batch_reach_one<2, LUT, COOP>(a, grid, block, smem, stg, st, per_sm);
+        case 4: return batch_reach_one<4, LUT, COOP>(a, grid, block, smem, stg, st, per_sm);
+        default: return batch_reach_one<8, LUT, COOP>(a, grid, block, smem, stg, st, per_sm);
+    }
+}
+
+cudaError_t batch_reach(const LaunchGroup &g, const BatchReachArgs &a, int grid, int block, size_t smem,
+                        uint32_t stg, cudaStream_t st, int *per_sm) {
+    if (g.coop) {
+        switch (g.mode) {
+            case kBRep16: return batch_reach_r<LutRep<true>, true>(g.R, a, grid, block, smem, stg, st, per_sm);
+            case kBRep32: return batch_reach_r<LutRep<false>, true>(g.R, a, grid, block, smem, stg, st, per_sm);
+            default: return batch_reach_r<LutPlain, true>(g.R, a, grid, block, smem, stg, st, per_sm);
+        }
+    }
+    switch (g.mode) {
+        case kBRep16: return batch_reach_r<LutRep<true>, false>(g.R, a, grid, block, smem, stg, st, per_sm);
+        case kBRep32: return batch_reach_r<LutRep<false>, false>(g.R, a, grid, block, smem, stg, st, per_sm);
+        default: return batch_reach_r<LutPlain, false>(g.R, a, grid, block, smem, stg, st, per_sm);
+    }
+}
+
+inline size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, uint32_t> g_tune_cache;   // (log2 |P|, log2 k, log2 C) -> chunk length
+
+int log2i(uint32_t v) {
+    int r = 0;
+    while ((1u << (r + 1)) <= v && r < 30) ++r;
+    return r;
+}
+
+}  // namespace
+}  // namespace ridfa
+
+struct ridfa_batch {
+    int device = -1;
+    std::vector<const ridfa_program *> progs;
+    std::vector<ridfa_batch_item> items;
+    uint8_t *d_accept = nullptr;
+    uint32_t chunk_len = 0;
+    bool use_graph = true;
+    // device state
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    std::vector<ridfa::LaunchGroup> groups;
+    ridfa::ProgDesc *d_progs = nullptr;
+    ridfa::TextDesc *d_texts = nullptr;
+    ridfa::TaskDesc *d_tasks = nullptr;
+    ridfa::SegDesc *d_segs = nullptr;
+    uint32_t *d_partials = nullptr, *d_tickets = nullptr, *d_flags = nullptr, *d_counters = nullptr,
+             *d_status = nullptr, *d_finals = nullptr;
+    ridfa::RunEntry *d_runs = nullptr;
+    uint32_t n_segs = 0, n_texts = 0, n_tasks = 0;
+    uint64_t total_bytes = 0, total_chunks = 0;
+    int grid = 0, block = 0;
+    std::vector<size_t> smem;
+    std::vector<uint32_t> stg;
+    std::vector<int> grids, blocks;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t *h_status = nullptr;
+};
+
+namespace ridfa {
+namespace {
+
+void batch_release(ridfa_batch *B) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+    if (B->dmem) cudaFree(B->dmem);
+    B->dmem = nullptr;
+}
+
+// Enqueue the whole batch (memsets, reach launches, join launch) on `st`.
+int batch_enqueue(ridfa_batch *B, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(B->d_counters, 0, 256, st);   // task tickets and status
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+        const LaunchGroup &g = B->groups[gi];
+        if (g.n_tasks == 0) continue;
+        BatchReachArgs a{B->d_progs, B->d_tasks + g.task0, g.n_tasks, 8, B->d_counters + gi, B->d_status,
+                         B->d_runs, B->d_finals};
+        e = batch_reach(g, a, B->grids[gi], B->blocks[gi], B->smem[gi], B->stg[gi], st, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (B->n_segs) {
+        BatchJoinArgs J{B->d_progs, B->d_texts, B->d_segs, B->d_partials, B->d_tickets, B->d_flags,
+                        B->d_accept, B->d_status};
+        rid_join_batch_kernel<<<B->n_segs, kBatchJoinThreads, 0, st>>>(J);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return RIDFA_OK;
+}
+
+// Plan and allocate the batch for chunk length L (items with n_chunks == 0 use ceil(len / L)).
+int batch_build(ridfa_batch *B, uint32_t L) {
+    batch_release(B);
+    B->blocks.clear();
+    B->stg.clear();
+    B->smem.clear();
+    B->grids.clear();
+    const uint32_t np = static_cast<uint32_t>(B->progs.size());
+    const uint32_t ni = static_cast<uint32_t>(B->items.size());
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device);
+    const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024 - 64;
+    // per-program device tables and layout
+    std::vector<const DeviceAutomaton *> dev(np, nullptr);
+    std::vector<uint32_t> mode(np, kBPlain), tis(np, 0);
+    std::vector<size_t> tbytes(np, 0);
+    for (uint32_t p = 0; p < np; ++p) {
+        const ridfa_program *P = B->progs[p];
+        std::lock_guard<std::mutex> lock(P->mu);
+        int err = RIDFA_OK;
+        dev[p] = device_copy(P, false, B->device, &err);
+        if (!dev[p]) return err;
+        const HostAutomaton &H = P->rid;
+        Automaton A{nullptr, nullptr, nullptr, nullptr, nullptr, H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+        const size_t r16 = LutRep<true>::smem_bytes(A), r32 = LutRep<false>::smem_bytes(A), pl = LutPlain::smem_bytes(A);
+        if (LutRep<true>::fits16(A) && r16 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep16; tbytes[p] = r16; }
+        else if (r32 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep32; tbytes[p] = r32; }
+        else if (pl + 8 * kWarpCoopBytes <= limit) { mode[p] = kBPlain; tis[p] = 1; tbytes[p] = pl; }
+        else { mode[p] = kBPlain; tis[p] = 0; tbytes[p] = 256; }
+    }
+    // texts grouped by program; chunk counts
+    std::vector<std::vector<uint32_t>> by_prog(np);
+    for (uint32_t i = 0; i < ni; ++i) by_prog[B->items[i].prog].push_back(i);
+    std::vector<TextDesc> texts;
+    std::vector<uint64_t> prog_chunks(np, 0);
+    std::vector<uint32_t> text0(np, 0);
+    bool aligned_all = true;
+    B->total_bytes = 0;
+    for (uint32_t p = 0; p < np; ++p) {
+        text0[p] = static_cast<uint32_t>(texts.size());
+        for (uint32_t i : by_prog[p]) {
+            const ridfa_batch_item &it = B->items[i];
+            TextDesc td{it.d_text, it.len, prog_chunks[p], 0, i};
+            if (it.len == 0) td.c = 0;
+            else if (it.n_chunks) td.c = it.n_chunks;
+            else td.c = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(it.len, (it.len + L - 1) / L)));
+            if (it.len && (reinterpret_cast<uintptr_t>(it.d_text) & 15)) aligned_all = false;
+            prog_chunks[p] += td.c;
+            B->total_bytes += it.len;
+            texts.push_back(td);
+        }
+    }
+    B->n_texts = static_cast<uint32_t>(texts.size());
+    B->total_chunks = 0;
+    for (uint32_t p = 0; p < np; ++p) B->total_chunks += prog_chunks[p];
+    // launch groups by layout; tasks ordered by group then program
+    B->groups.clear();
+    std::vector<TaskDesc> tasks;
+    for (uint32_t m = kBPlain; m <= kBRep32; ++m) {
+        LaunchGroup g;
+        g.mode = m;
+        g.coop = aligned_all;
+        for (uint32_t p = 0; p < np; ++p)
+            if (mode[p] == m && prog_chunks[p]) {
+                g.progs.push_back(p);
+                const uint32_t k = B->progs[p]->rid.k;
+                g.R = std::max(g.R, k <= 32 ? 1 : k <= 64 ? 2 : k <= 128 ? 4 : 8);
+                g.table_smem = std::max(g.table_smem, tbytes[p]);
+            }
+        if (g.progs.empty()) continue;
+        g.task0 = static_cast<uint32_t>(tasks.size());
+        const int cap = g.R <= 4 ? 1024 : 512;
+        const uint32_t stg = static_cast<uint32_t>((g.table_smem + 127) & ~static_cast<size_t>(127));
+        int warps = g.coop ? static_cast<int>(std::min<size_t>(cap / 32, (limit - stg) / kWarpCoopBytes)) : cap / 32;
+        warps = std::max(warps, 1);
+        const uint64_t per_task = 32ull * warps;
+        for (uint32_t p : g.progs)
+            for (uint64_t c0 = 0; c0 < prog_chunks[p]; c0 += per_task)
+                tasks.push_back(TaskDesc{c0, p, static_cast<uint32_t>(std::min<uint64_t>(per_task, prog_chunks[p] - c0))});
+        g.n_tasks = static_cast<uint32_t>(tasks.size()) - g.task0;
+        B->groups.push_back(g);
+        B->blocks.push_back(warps * 32);
+        B->stg.push_back(stg);
+        B->smem.push_back(g.coop ? stg + static_cast<size_t>(warps) * kWarpCoopBytes : g.table_smem);
+    }
+    B->n_tasks = static_cast<uint32_t>(tasks.size());
+    // join segments
+    std::vector<SegDesc> segs;
+    for (uint32_t t = 0; t < B->n_texts; ++t) {
+        const TextDesc &td = texts[t];
+        uint32_t prog = 0;
+        for (uint32_t p = 0; p < np; ++p)
+            if (t >= text0[p] && t < text0[p] + by_prog[p].size()) prog = p;
+        const uint64_t nb = td.c > 1 ? td.c - 1 : 0;
+        const uint32_t nseg = nb ? static_cast<uint32_t>((nb + kBatchJoinThreads - 1) / kBatchJoinThreads) : 1;
+        const uint32_t part0 = static_cast<uint32_t>(segs.size());
+        for (uint32_t sgi = 0; sgi < nseg; ++sgi) {
+            const uint64_t b0 = 1 + static_cast<uint64_t>(sgi) * kBatchJoinThreads;
+            const uint32_t cnt = nb ? static_cast<uint32_t>(std::min<uint64_t>(kBatchJoinThreads, nb + 1 - b0)) : 0;
+            segs.push_back(SegDesc{b0, prog, t, cnt, sgi, nseg, part0});
+        }
+    }
+    B->n_segs = static_cast<uint32_t>(segs.size());
+    // launch shapes: one block per SM (as many as fit), persistent; the groups run one after
+    // another, so they share one run list sized for the largest
+    B->grids.assign(B->groups.size(), 0);
+    uint64_t run_warps = 0;
+    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+        int per_sm = 0;
+        BatchReachArgs a{};
+        cudaError_t eo = batch_reach(B->groups[gi], a, 0, B->blocks[gi], B->smem[gi], B->stg[gi], nullptr, &per_sm);
+        if (eo != cudaSuccess) return cuda_fail(eo);
+        if (per_sm < 1) return RIDFA_E_UNSUPPORTED;
+        B->grids[gi] = static_cast<int>(std::min<uint64_t>(B->groups[gi].n_tasks, static_cast<uint64_t>(sms) * per_sm));
+        run_warps = std::max<uint64_t>(run_warps, static_cast<uint64_t>(B->grids[gi]) * (B->blocks[gi] / 32));
+    }
+    // one device allocation
+    uint64_t maps_bytes = 0, dinfo_bytes = 0;
+    std::vector<uint64_t> maps_off(np), dinfo_off(np);
+    for (uint32_t p = 0; p < np; ++p) {
+        maps_off[p] = maps_bytes;
+        dinfo_off[p] = dinfo_bytes;
+        maps_bytes += al256(prog_chunks[p] * B->progs[p]->rid.k * 2);
+        dinfo_bytes += al256(prog_chunks[p] * 4);
+    }
+    size_t off = 0;
+    const size_t o_counters = off; off += 256;
+    const size_t o_progs = off;    off += al256(np * sizeof(ProgDesc));
+    const size_t o_texts = off;    off += al256(texts.size() * sizeof(TextDesc));
+    const size_t o_tasks = off;    off += al256(tasks.size() * sizeof(TaskDesc));
+    const size_t o_segs = off;     off += al256(segs.size() * sizeof(SegDesc));
+    const size_t o_part = off;     off += al256(segs.size() * kPartialWords * 4);
+    const size_t o_tick = off;     off += al256(texts.size() * 4);
+    const size_t o_flags = off;    off += al256(texts.size() * 4);
+    const size_t o_runs = off;     off += al256(run_warps * kRunsPerWarp * sizeof(RunEntry));
+    const size_t o_finals = off;   off += al256(run_warps * kFinalsPerWarp * 4);
+    const size_t o_maps = off;     off += maps_bytes;
+    const size_t o_dinfo = off;    off += dinfo_bytes;
+    cudaError_t e = cudaMalloc(&B->dmem, off);
+    if (e != cudaSuccess) return cuda_fail(e);
+    B->dbytes = off;
+    uint8_t *base = static_cast<uint8_t *>(B->dmem);
+    B->d_counters = reinterpret_cast<uint32_t *>(base + o_counters);
+    B->d_status = B->d_counters + 32;
+    B->d_progs = reinterpret_cast<ProgDesc *>(base + o_progs);
+    B->d_texts = reinterpret_cast<TextDesc *>(base + o_texts);
+    B->d_tasks = reinterpret_cast<TaskDesc *>(base + o_tasks);
+    B->d_segs = reinterpret_cast<SegDesc *>(base + o_segs);
+    B->d_partials = reinterpret_cast<uint32_t *>(base + o_part);
+    B->d_tickets = reinterpret_cast<uint32_t *>(base + o_tick);
+    B->d_flags = reinterpret_cast<uint32_t *>(base + o_flags);
+    B->d_runs = reinterpret_cast<RunEntry *>(base + o_runs);
+    B->d_finals = reinterpret_cast<uint32_t *>(base + o_finals);
+    std::vector<ProgDesc> pd(np);
+    for (uint32_t p = 0; p < np; ++p) {
+        const HostAutomaton &H = B->progs[p]->rid;
+        const DeviceAutomaton *D = dev[p];
+        pd[p].A = Automaton{D->trans, D->classmap, D->final_bits, D->ifmask, D->slot_state,
+                            H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+        pd[p].texts = B->d_texts + text0[p];
+        pd[p].maps = reinterpret_cast<uint16_t *>(base + o_maps + maps_off[p]);
+        pd[p].dinfo = reinterpret_cast<uint32_t *>(base + o_dinfo + dinfo_off[p]);
+        pd[p].n_texts = static_cast<uint32_t>(by_prog[p].size());
+        pd[p].tis = tis[p];
+        pd[p].text0 = text0[p];
+    }
+    e = cudaMemset(base, 0, o_maps);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_progs, pd.data(), np * sizeof(ProgDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !texts.empty()) e = cudaMemcpy(B->d_texts, texts.data(), texts.size() * sizeof(TextDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !tasks.empty()) e = cudaMemcpy(B->d_tasks, tasks.data(), tasks.size() * sizeof(TaskDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !segs.empty()) e = cudaMemcpy(B->d_segs, segs.data(), segs.size() * sizeof(SegDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // capture into a graph
+    if (B->use_graph) {
+        cudaStream_t cs;
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int err = e == cudaSuccess ? batch_enqueue(B, cs) : cuda_fail(e);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (err != RIDFA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return err;
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2);
+        B->graph = g;
+        e = cudaGraphInstantiate(&B->exec, g, 0);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return RIDFA_OK;
+}
+
+int batch_run(ridfa_batch *B, cudaStream_t st) {
+    if (B->exec) {
+        cudaError_t e = cudaGraphLaunch(B->exec, st);
+        return e == cudaSuccess ? RIDFA_OK : cuda_fail(e);
+    }
+    return batch_enqueue(B, st);
+}
+
+// Chunk length for the batch.  Every program is keyed by (log2 |P|, log2 k, log2 C); when all
+// keys are in the cache and agree, that length is used.  Otherwise candidate lengths are timed
+// on the batch itself (3 replays each, CUDA events) and the winner is recorded under every key.
+int batch_autotune(ridfa_batch *B, uint32_t *out_len) {
+    std::vector<std::tuple<int, int, int>> keys;
+    for (const ridfa_program *P : B->progs)
+        keys.emplace_back(log2i(P->rid.n_states), log2i(P->rid.k), log2i(P->rid.n_classes));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        uint32_t v = 0;
+        bool all = true;
+        for (auto &k : keys) {
+            auto it = g_tune_cache.find(k);
+            if (it == g_tune_cache.end() || (v && it->second != v)) {
+                all = false;
+                break;
+            }
+            v = it->second;
+        }
+        if (all && v) {
+            *out_len = v;
+            return RIDFA_OK;
+        }
+    }
+    const uint32_t cands[] = {4096, 8192, 16384, 32768};
+    float best = 1e30f;
+    uint32_t best_len = 8192;
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int err = RIDFA_OK;
+    for (uint32_t L : cands) {
+        err = batch_build(B, L);
+        if (err != RIDFA_OK) break;
+        batch_run(B, st);                       // warm-up
+        cudaEventRecord(a, st);
+        for (int r = 0; r < 3; ++r) batch_run(B, st);
+        cudaEventRecord(b, st);
+        e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) {
+            err = cuda_fail(e);
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) {
+            best = ms;
+            best_len = L;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(st);
+    if (err != RIDFA_OK) return err;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto &k : keys) g_tune_cache[k] = best_len;
+    }
+    *out_len = best_len;
+    return RIDFA_OK;
+}
+
+}  // namespace
+}  // namespace ridfa
+
+extern "C" int ridfa_batch_create(const ridfa_program *const *progs, uint32_t n_progs,
+                                  const ridfa_batch_item *items, uint32_t n_items, uint8_t *d_accept,
+                                  const ridfa_batch_opts *opts, ridfa_batch **out) {
+    if (!progs || !n_progs || !items || !n_items || !d_accept || !out) return RIDFA_E_ARG;
+    for (uint32_t p = 0; p < n_progs; ++p) {
+        if (!progs[p]) return RIDFA_E_ARG;
+        if (progs[p]->rid.k > RIDFA_MAX_SLOTS) return RIDFA_E_UNSUPPORTED;
+    }
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const ridfa_batch_item &it = items[i];
+        if (it.prog >= n_progs || (it.len && !it.d_text)) return RIDFA_E_ARG;
+        if (it.n_chunks > it.len || (it.len == 0 && it.n_chunks)) return RIDFA_E_CHUNKS;
+    }
+    ridfa_batch *B = new (std::nothrow) ridfa_batch();
+    if (!B) return RIDFA_E_NOMEM;
+    if (cudaGetDevice(&B->device) != cudaSuccess) {
+        delete B;
+        return ridfa::cuda_fail(cudaGetLastError());
+    }
+    B->progs.assign(progs, progs + n_progs);
+    B->items.assign(items, items + n_items);
+    B->d_accept = d_accept;
+    B->use_graph = !(opts && opts->no_graph);
+    uint32_t L = opts ? opts->chunk_len : 0;
+    int err = RIDFA_OK;
+    if (L == 0) err = ridfa::batch_autotune(B, &L);
+    if (err == RIDFA_OK) err = ridfa::batch_build(B, L);
+    if (err != RIDFA_OK) {
+        ridfa::batch_release(B);
+        delete B;
+        return err;
+    }
+    B->chunk_len = L;
+    *out = B;
+    return RIDFA_OK;
+}
+
+extern "C" int ridfa_batch_run(ridfa_batch *b, void *stream) {
+    if (!b) return RIDFA_E_ARG;
+    return ridfa::batch_run(b, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ridfa_batch_get_stats(const ridfa_batch *b, ridfa_batch_stats *out) {
+    if (!b || !out) return RIDFA_E_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->total_bytes = b->total_bytes;
+    out->total_chunks = b->total_chunks;
+    out->n_programs = static_cast<uint32_t>(b->progs.size());
+    out->n_launches = static_cast<uint32_t>(b->groups.size()) + (b->n_segs ? 1 : 0);
+    out->n_tasks = b->n_tasks;
+    out->n_segments = b->n_segs;
+    out->chunk_len = b->chunk_len;
+    out->graph = b->exec ? 1 : 0;
+    out->device_bytes = b->dbytes;
+    return RIDFA_OK;
+}
+
+extern "C" void ridfa_batch_free(ridfa_batch *b) {
+    if (!b) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    ridfa::batch_release(b);
+    cudaSetDevice(cur);
+    (void)cudaGetLastError();
+    delete b;
+}
+
+extern "C" int ridfa_recognize_batch(const ridfa_program *const *progs, uint32_t n_progs,
+                                     const ridfa_batch_item *items, uint32_t n_items, uint8_t *d_accept,
+                                     void *stream) {
+    ridfa_batch_opts o{8192, 1, {0, 0}};   // one run: no graph
+    ridfa_batch *b = nullptr;
+    int err = ridfa_batch_create(progs, n_progs, items, n_items, d_accept, &o, &b);
+    if (err != RIDFA_OK) return err;
+    err = ridfa_batch_run(b, stream);
+    if (err == RIDFA_OK && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        err = ridfa::cuda_fail(cudaGetLastError());
+    ridfa_batch_free(b);
+    return err;
+}

@@ -29,244 +29,64 @@
 #include <vector>
 
 #include "ridfa_internal.h"
+#include "ridfa_kernels.cuh"
 
 namespace ridfa {
+// --------------------------------------------------------------------------- host side
+int cuda_fail(cudaError_t e) {
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? RIDFA_E_NOMEM : RIDFA_E_CUDA;
+}
+
+int upload(const HostAutomaton &H, DeviceAutomaton &D, int dev) {
+    D.device = dev;
+    const size_t bt = H.trans.size() * 2, bf = H.final_bits.size() * 4, bi = H.ifmask.size() * 4,
+                 bs = H.slot_state.size() * 2;
+    auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+    const size_t total = al(bt) + al(256) + al(bf) + al(bi) + al(bs);
+    uint8_t *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, total);
+    if (e != cudaSuccess) return cuda_fail(e);
+    size_t off = 0;
+    D.trans = reinterpret_cast<uint16_t *>(base + off); off += al(bt);
+    D.classmap = base + off; off += al(256);
+    D.final_bits = reinterpret_cast<uint32_t *>(base + off); off += al(bf);
+    D.ifmask = reinterpret_cast<uint32_t *>(base + off); off += al(bi);
+    D.slot_state = reinterpret_cast<uint16_t *>(base + off); off += al(bs);
+    D.bytes = total;
+    e = cudaMemcpy(D.trans, H.trans.data(), bt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(D.classmap, H.classmap.data(), 256, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && bf) e = cudaMemcpy(D.final_bits, H.final_bits.data(), bf, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && bi) e = cudaMemcpy(D.ifmask, H.ifmask.data(), bi, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && bs) e = cudaMemcpy(D.slot_state, H.slot_state.data(), bs, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        D = DeviceAutomaton{};
+        return cuda_fail(e);
+    }
+    return RIDFA_OK;
+}
+
+const DeviceAutomaton *device_copy(const ridfa_program *P, bool dfa, int dev, int *err) {
+    auto &vec = dfa ? P->dev_dfa : P->dev_rid;
+    for (auto &d : vec)
+        if (d.device == dev) return &d;
+    DeviceAutomaton D;
+    *err = upload(dfa ? P->dfa : P->rid, D, dev);
+    if (*err != RIDFA_OK) return nullptr;
+    vec.push_back(D);
+    return &vec.back();
+}
+
+int smem_optin_limit() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+
 namespace {
-
-constexpr uint32_t kFull = 0xFFFFFFFFu;
-constexpr uint16_t kUndef = 0xFFFF;
-constexpr uint32_t kStatusWide = 1u;      // some chunk has > 32 distinct end states
-constexpr uint32_t kStatusBad = 2u;       // a device consistency check failed
-constexpr int kMaxD = 32;                 // distinct end states handled by the matrix join
-constexpr int kJoinThreads = 256;
-static_assert(kPartialWords == 1 + kMaxD, "join partial layout");
-
-struct Automaton {            // device view of one automaton
-    const uint16_t *trans;    // [(n+1) * C]
-    const uint8_t *classmap;  // [256]
-    const uint32_t *final_bits;
-    const uint32_t *ifmask;   // [(n+1) * kw]
-    const uint16_t *slot_state;
-    uint32_t n, C, k, kw, q0_slot;
-};
-
-__host__ __device__ inline uint64_t chunk_begin(uint64_t i, uint64_t len, uint64_t c) {
-    // floor(i * len / c) without 128-bit products: i*(len/c) + (i*(len%c))/c
-    return i * (len / c) + (i * (len % c)) / c;
-}
-
-// ------------------------------------------------------------------------------ reach
-struct ReachArgs {
-    Automaton A;
-    const uint8_t *text;
-    uint64_t len;
-    uint32_t c;
-    uint16_t *maps;           // [c][k]
-    uint32_t *dinfo;          // [c]: (m << 16) | min defined end state (0xFFFF if none)
-    uint32_t *status;
-    uint32_t probe;
-};
-
-__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
-}
-__device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
-    uint16_t v;
-    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
-    return v;
-}
-__device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
-}
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Text staging for the converged phase (TMA path): every lane streams its own chunk through a
-// ring of kStages windows of kWin bytes in shared memory, filled by 1-D bulk copies
-// (cp.async.bulk) that complete on one mbarrier per warp and stage.  A lane's window buffers
-// are kLaneStride bytes apart, so the 16-byte reads of 8 consecutive lanes fall in 8 different
-// bank groups (stride 48 = 3 granules, and 3 is odd).
-constexpr uint32_t kWin = 128;
-constexpr uint32_t kStages = 2;
-constexpr uint32_t kLaneStride = 144;
-// per-warp ring + barriers, rounded to 16 bytes so every warp's ring starts 16-byte aligned
-// (bulk-copy destinations must be)
-constexpr uint32_t kWarpStageBytes = (kStages * 32 * kLaneStride + kStages * 8 + 15) & ~15u;
-static_assert(kWarpStageBytes % 16 == 0 && (kStages * 32 * kLaneStride) % 16 == 0 && kLaneStride % 16 == 0,
-              "bulk-copy destinations must stay 16-byte aligned");
-constexpr uint32_t kStatusTimeout = 4u;   // a bounded wait on a copy gave up
-// text paths of the converged phase
-constexpr int kPathGlobal = 0;   // each lane: 16-byte global loads of its own chunk
-constexpr int kPathBulk = 1;     // each lane: 1-D bulk copies into a shared-memory ring
-constexpr int kPathCoop = 2;     // the warp: coalesced loads of 8 chunks' windows per instruction
-constexpr int kPathCoop2 = 3;    // the same with two chunks per lane, interleaved
-// cooperative path: one 64-byte window per chunk of the warp; granule g of chunk j's window sits
-// at 16-byte unit 4j + (g ^ ((j >> 1) & 3)), so both the stores (lanes write 4 granules of 2
-// chunks per 8-lane phase) and the owners' 16-byte reads (8 chunks, one granule each) are
-// conflict-free
-constexpr uint32_t kCoopWin = 64;
-constexpr uint32_t kCoopBufBytes = 32 * kCoopWin;          // one round: a window per chunk
-constexpr uint32_t kWarpCoopBytes = 2 * kCoopBufBytes;     // double-buffered
-
-__device__ __forceinline__ void cp_async_16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ uint32_t coop_unit(uint32_t j, uint32_t g) { return 4 * j + (g ^ ((j >> 1) & 3)); }
-constexpr uint32_t kSpinLimit = 1u << 24;
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t tx) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P1;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, P1;\n\t}"
-        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ uint4 lds_v4(uint32_t addr) {
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
-    return v;
-}
-__device__ __forceinline__ uint32_t lds_u8(uint32_t addr) {
-    uint16_t v;
-    asm volatile("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(addr));
-    return v;
-}
-
-// Table lookup policies.  A run's state is kept in the policy's own encoding (`enc`); `id`
-// recovers the automaton state number.
-//
-// Plain: compact uint16 table [(n+1) * C] and uint8 class map, in shared memory (or global
-// memory when it does not fit).  Lanes gathering different entries may hit the same bank.
-struct LutPlain {
-    const uint16_t *t;
-    const uint8_t *cls;
-    uint32_t C;
-    static size_t smem_bytes(const Automaton &A) { return 256 + static_cast<size_t>(A.n + 1) * A.C * 2; }
-    __device__ void setup(const Automaton &A, uint8_t *smem, bool table_in_smem) {
-        uint8_t *s_cls = smem;
-        uint16_t *s_t = reinterpret_cast<uint16_t *>(smem + 256);
-        for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_cls[i] = A.classmap[i];
-        if (table_in_smem)
-            for (uint32_t i = threadIdx.x; i < (A.n + 1) * A.C; i += blockDim.x) s_t[i] = A.trans[i];
-        t = table_in_smem ? s_t : A.trans;
-        cls = s_cls;
-        C = A.C;
-    }
-    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id; }
-    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s; }
-    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return cls[b]; }
-    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return t[s * C + c]; }
-};
-
-// Lane-replicated tables: every entry is stored 32 times, lane l's copy in bank l, so a warp's
-// 32 gathers are always one shared-memory wavefront whatever states and bytes the lanes hold.
-// Entries hold byte offsets, so a step is one add and one load:
-//   class table, 32-bit words: word (b * 32 + l) = class offset of byte b;
-//   Rep16 transition table, 16-bit halves: entry (s, c) at byte
-//       (s * Cp/2 + c/2) * 128 + l * 4 + (c & 1) * 2,   value = state offset s' * Cp * 64;
-//   Rep32 transition table, 32-bit words: entry (s, c) at word (s * C + c) * 32 + l,
-//       value = s' * C * 128.
-template <bool W16>
-struct LutRep {
-    uint32_t lc, lt;          // shared addresses of this lane's class / transition copies
-    uint32_t row;             // state offset stride
-    __host__ __device__ static uint32_t cpad(const Automaton &A) { return W16 ? (A.C + 1) & ~1u : A.C; }
-    static size_t smem_bytes(const Automaton &A) {
-        return 256 * 128 + static_cast<size_t>(A.n + 1) * cpad(A) * (W16 ? 64 : 128);
-    }
-    static bool fits16(const Automaton &A) {
-        return static_cast<uint64_t>(A.n) * cpad(A) * 64 + 128 * ((cpad(A) - 1) / 2) + 2 <= 0xFFFF;
-    }
-    __device__ __forceinline__ uint32_t cls_off(uint32_t c) const {
-        return W16 ? (c >> 1) * 128 + (c & 1) * 2 : c * 128;
-    }
-    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
-        const uint32_t Cp = cpad(A);
-        row = W16 ? Cp * 64 : Cp * 128;
-        const uint32_t base_c = smem_addr(smem);
-        const uint32_t base_t = base_c + 256 * 128;
-        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x)
-            sts_u32(base_c + i * 4, cls_off(A.classmap[i >> 5]));
-        const uint32_t words = W16 ? (A.n + 1) * Cp / 2 : (A.n + 1) * Cp;
-        for (uint32_t i = threadIdx.x; i < words * 32; i += blockDim.x) {
-            const uint32_t w = i >> 5;
-            uint32_t v;
-            if (W16) {
-                const uint32_t s = (2 * w) / Cp, c0 = (2 * w) % Cp;
-                const uint32_t n0 = A.trans[s * A.C + c0];
-                const uint32_t n1 = (c0 + 1 < A.C) ? A.trans[s * A.C + c0 + 1] : A.n;
-                v = (n0 * row) | ((n1 * row) << 16);
-            } else {
-                v = A.trans[w] * row;
-            }
-            sts_u32(base_t + i * 4, v);
-        }
-        const uint32_t lane = threadIdx.x & 31;
-        lc = base_c + lane * 4;
-        lt = base_t + lane * 4;
-    }
-    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id * row; }
-    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s / row; }
-    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
-    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const {
-        return W16 ? lds_u16(lt + s + c) : lds_u32(lt + s + c);
-    }
-};
-
-// Chunk-map row of one chunk written by one lane: entries of alive slots get `val`.
-template <int R>
-__device__ __forceinline__ void write_row(uint16_t *row, uint32_t k, const uint32_t (&alive)[R],
-                                          uint16_t val) {
-    if ((k & 1) == 0) {
-        uint32_t *row32 = reinterpret_cast<uint32_t *>(row);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t m = alive[r];
-            for (uint32_t l = 0; l < 32; l += 2) {
-                const uint32_t a = r * 32 + l;
-                if (a >= k) break;
-                const uint32_t lo = ((m >> l) & 1) ? val : kUndef;
-                const uint32_t hi = ((m >> (l + 1)) & 1) ? val : kUndef;
-                row32[a >> 1] = lo | (hi << 16);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t m = alive[r];
-            for (uint32_t l = 0; l < 32; ++l) {
-                const uint32_t a = r * 32 + l;
-                if (a >= k) break;
-                row[a] = ((m >> l) & 1) ? val : kUndef;
-            }
-        }
-    }
-}
 
 template <int R, class LUT, int BLOCK, int PATH>
 __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int table_in_smem,
@@ -275,7 +95,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
     const Automaton &A = p.A;
     LUT T;
     T.setup(A, smem, table_in_smem != 0);
-    // per-warp staging ring and its mbarriers (TMA path only)
+    // per-warp staging ring and its mbarriers (bulk-copy path only)
     const uint32_t warp_in_block = threadIdx.x >> 5;
     const uint32_t stg_base = smem_addr(smem) + staging_offset +
                               warp_in_block * (PATH == kPathCoop ? kWarpCoopBytes : kWarpStageBytes);
@@ -294,6 +114,9 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
     const uint64_t n_tasks = (static_cast<uint64_t>(p.c) + 31) / 32;
     const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    RunEntry *wruns = p.runs ? p.runs + warp0 * kRunsPerWarp : nullptr;
+    uint32_t *wfin = p.finals ? p.finals + warp0 * kFinalsPerWarp : nullptr;   // null with wruns
+    uint32_t *wball = wfin ? wfin + kRunsPerWarp : nullptr;
 
     // slot start states of this lane (slot a = r*32 + lane)
     uint32_t start_state[R];
@@ -307,280 +130,183 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
 
     for (uint64_t task = warp0; task < n_tasks; task += n_warps) {
         const uint64_t chunk0 = task * 32;
-        uint64_t my_pos = 0;
-        uint32_t my_state = dead;
-        uint32_t my_alive[R];
-        bool my_pending = false;
-#pragma unroll
-        for (int r = 0; r < R; ++r) my_alive[r] = 0;
-
         // ---------------- speculative phase, one chunk at a time, lanes = runs
+        // A chunk whose live runs reduce to m <= kMaxRun distinct states hands them off as m
+        // runs; without a run list (no scratch) only m = 1, kept by lane j.
+        uint32_t my_hand = 0;         // owner lane j of a handed-off chunk: (m << 16) | first run
+        uint32_t nruns = 0, handed = 0;
+        uint32_t amask[R];            // bit j: this lane's slot of register r alive at chunk j's hand-off
+#pragma unroll
+        for (int r = 0; r < R; ++r) amask[r] = 0;
+        uint64_t one_pos = 0;
+        uint32_t one_state = dead;
         for (uint32_t j = 0; j < 32; ++j) {
             const uint64_t ch = chunk0 + j;
             if (ch >= p.c) break;
             const uint64_t beg = chunk_begin(ch, p.len, p.c);
             const uint64_t end = chunk_begin(ch + 1, p.len, p.c);
-            uint32_t s[R];
+            uint32_t d, alive[R];
+            uint64_t hp = 0;
+            const int m = speculate<R, LUT>(T, A, p.text, beg, end, p.probe, lane, start_state, start_live, dead,
+                                            p.maps + ch * A.k, p.dinfo + ch, p.status, wruns != nullptr,
+                                            wruns == nullptr, &hp, &d, alive);
+            if (m >= 1) {
+                handed |= 1u << j;
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[r] = start_state[r];
-            uint32_t live_regs = start_live;       // registers holding at least one live run
-            uint64_t pos = beg;
-            bool converged = false;
-            uint32_t conv_state = dead;
-            while (pos < end) {
-                const uint64_t stop = min(end, pos + p.probe);
-                for (; pos < stop; ++pos) {
-                    const uint32_t c = T.cls_of(__ldg(p.text + pos));
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (live_regs & (1u << r)) s[r] = T.next(s[r], c);
-                }
-                // convergence: are all live runs in one state?  (dead runs are dropped)
-                uint32_t lo = 0xFFFFFFFFu, hi = 0;
-                live_regs = 0;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (__any_sync(kFull, s[r] != dead)) live_regs |= 1u << r;
-                    if (s[r] != dead) {
-                        lo = min(lo, s[r]);
-                        hi = max(hi, s[r]);
+                for (int r = 0; r < R; ++r) amask[r] |= ((alive[r] >> lane) & 1u) << j;
+                if (wruns) {
+                    if (lane < static_cast<uint32_t>(m))
+                        wruns[nruns + lane] = RunEntry{hp, d, static_cast<uint16_t>(j), static_cast<uint16_t>(lane)};
+                    if (lane == j) {
+                        my_hand = (static_cast<uint32_t>(m) << 16) | nruns;
                     }
-                }
-                lo = __reduce_min_sync(kFull, lo);
-                hi = __reduce_max_sync(kFull, hi);
-                if (lo == 0xFFFFFFFFu || lo == hi) {
-                    converged = true;
-                    conv_state = (lo == 0xFFFFFFFFu) ? dead : lo;
-                    break;
+                    nruns += static_cast<uint32_t>(m);
+                } else if (lane == j) {
+                    my_hand = (1u << 16) | j;
+                    one_pos = hp;
+                    one_state = d;
                 }
             }
-            uint16_t *row = p.maps + ch * A.k;
-            if (converged && pos < end && conv_state != dead) {
-                // hand the single surviving run to lane j
+        }
+        // the alive bits wait in the finals area while the runs go on (registers are scarce
+        // there); without it the rows carry tags instead
+        if (wball) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t b = __ballot_sync(kFull, s[r] != dead);
-                    if (lane == j) my_alive[r] = b;
-                }
-                if (lane == j) {
-                    my_pos = pos;
-                    my_state = conv_state;
-                    my_pending = true;
+            for (int r = 0; r < R; ++r) wball[r * 32 + lane] = amask[r];
+        }
+        __syncwarp();
+
+        // ---------------- converged phase: each lane finishes one run (rounds of 32 runs)
+        const uint32_t total_runs = wruns ? nruns : 32;
+        uint32_t fin_reg = dead;      // final state of run `lane` when there are at most 32 runs
+        for (uint32_t rb = 0; rb < total_runs; rb += 32) {
+            bool my_pending;
+            uint64_t pos = 0, end = 0;
+            uint32_t s = dead, jj = lane;
+            const uint32_t idx = rb + lane;
+            if (wruns) {
+                my_pending = idx < nruns;
+                if (my_pending) {
+                    const RunEntry e = wruns[idx];
+                    pos = e.pos;
+                    s = e.state;
+                    jj = e.chunk;
                 }
             } else {
-                // finished in the speculative phase: write the row (coalesced) and D_i's size
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t a = r * 32 + lane;
-                    if (a < A.k) row[a] = s[r] == dead ? kUndef : static_cast<uint16_t>(T.id(s[r]));
-                }
-                uint32_t cnt = 0, first = kUndef, cur = 0;
-                bool more = true;
-                while (more) {
-                    uint32_t v = 0xFFFFFFFFu;
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (s[r] != dead && (cnt == 0 || s[r] > cur)) v = min(v, s[r]);
-                    v = __reduce_min_sync(kFull, v);
-                    if (v == 0xFFFFFFFFu) {
-                        more = false;
-                    } else {
-                        if (cnt == 0) first = T.id(v);
-                        cur = v;
-                        if (++cnt > kMaxD) more = false;
-                    }
-                }
-                if (lane == 0) {
-                    if (cnt > kMaxD) {
-                        p.dinfo[ch] = (0xFFu << 16) | first;
-                        atomicOr(p.status, kStatusWide);
-                    } else {
-                        p.dinfo[ch] = (cnt << 16) | first;
-                    }
-                }
+                my_pending = my_hand != 0;
+                pos = one_pos;
+                s = one_state;
             }
-        }
-
-        // ---------------- converged phase: each lane finishes its own chunk's single run
-        uint64_t pos = my_pos, end = 0;
-        uint32_t s = my_state;
-        if (my_pending) end = chunk_begin(chunk0 + lane + 1, p.len, p.c);
-        if (PATH == kPathCoop && __any_sync(kFull, my_pending)) {
-            // windows [wb + 64r, +64) of each chunk (wb = the 16-byte boundary at or below the
-            // resume position); bytes at or past `lim` (len rounded down to 16) use plain loads.
-            // Lane l copies granule (l & 3) of the windows of chunks (l >> 2) + 8u, u = 0..3, with
-            // cp.async (L2 -> shared memory, no register or L1 round trip): 8 chunks' windows per
-            // instruction, one round ahead, double-buffered.
-            const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
-            const uint64_t stop = min(end, lim);
-            const uint64_t wb = pos & ~static_cast<uint64_t>(15);
-            const uint32_t nwin = (my_pending && wb < stop)
-                                      ? static_cast<uint32_t>((stop - wb + kCoopWin - 1) / kCoopWin) : 0;
-            const uint32_t g = lane & 3;
-            const uint32_t max_win = __reduce_max_sync(kFull, nwin);
-            auto issue = [&](uint32_t r) {
-                const uint32_t buf = stg_base + (r & 1) * kCoopBufBytes;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = u * 8 + (lane >> 2);        // chunk whose granule g this lane copies
-                    const uint64_t a = __shfl_sync(kFull, wb, j) + static_cast<uint64_t>(kCoopWin) * r + 16 * g;
-                    const uint32_t nw = __shfl_sync(kFull, nwin, j);
-                    if (r < nw && a + 16 <= lim) cp_async_16(buf + 16 * coop_unit(j, g), p.text + a);
-                }
-                cp_async_commit();
-            };
-            issue(0);
-            const uint32_t sw = (lane >> 1) & 3;
-            for (uint32_t r = 0; r < max_win; ++r) {
-                if (r + 1 < max_win) issue(r + 1);
-                else cp_async_commit();               // keep one group per round
-                cp_async_wait1();                     // this lane's copies of round r have landed
-                __syncwarp();                         // ... and every other lane's
-                const uint64_t ws = wb + static_cast<uint64_t>(kCoopWin) * r;
-                if (r < nwin && s != dead) {
-                    const uint32_t sb = stg_base + (r & 1) * kCoopBufBytes + 64 * lane;
-                    const uint64_t lo = max(pos, ws), hi = min(stop, ws + kCoopWin);
-                    if (lo == ws && hi == ws + kCoopWin) {
-#pragma unroll
-                        for (uint32_t q16 = 0; q16 < kCoopWin / 16; ++q16) {
-                            const uint4 x = lds_v4(sb + 16 * (q16 ^ sw));
-                            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-                            uint32_t cl[16];
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
-                        }
-                    } else {
-                        for (uint64_t q = lo; q < hi; ++q) {
-                            const uint32_t o = static_cast<uint32_t>(q - ws);
-                            s = T.next(s, T.cls_of(lds_u8(sb + 16 * ((o >> 4) ^ sw) + (o & 15))));
-                        }
-                    }
-                    pos = hi;
-                }
-                __syncwarp();                         // buffer (r & 1) is refilled next round
-            }
-            cp_async_wait0();
-            __syncwarp();
-        }
-        if (PATH == kPathBulk) {
-            if (__any_sync(kFull, my_pending) && !failed) {
-                // windows [ws0 + kWin*j, +kWin) of the 16-byte-aligned text; bytes at or past
-                // `lim` (the text length rounded down to 16) are left to plain loads below
+            if (my_pending) end = chunk_begin(chunk0 + jj + 1, p.len, p.c);
+            if (PATH == kPathCoop && __any_sync(kFull, my_pending)) {
                 const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
-                const uint64_t ws0 = pos & ~static_cast<uint64_t>(15);
-                const uint64_t stop = min(end, lim);
-                uint32_t j_issue = 0, j_read = 0;
-                auto issue = [&]() {
-                    const uint32_t stage = wctr % kStages;
-                    const uint32_t bar = bar_base + stage * 8;
-                    const uint64_t ws = ws0 + static_cast<uint64_t>(kWin) * j_issue;
-                    uint32_t bytes = 0;
-                    if (my_pending && s != dead && ws < stop)
-                        bytes = static_cast<uint32_t>(min(static_cast<uint64_t>(kWin), lim - ws));
-                    const uint32_t total = __reduce_add_sync(kFull, bytes);
-                    if (lane == 0) mbar_arrive_expect_tx(bar, total);
-                    __syncwarp();
-                    if (bytes)
-                        bulk_copy_g2s(stg_base + (stage * 32 + lane) * kLaneStride, p.text + ws, bytes, bar);
-                    ++wctr;
-                    ++j_issue;
-                };
-                auto wait_stage = [&]() -> bool {
-                    const uint32_t bar = bar_base + (rctr % kStages) * 8;
-                    const uint32_t parity = (rctr / kStages) & 1;
-                    for (uint32_t it = 0; it < kSpinLimit; ++it)
-                        if (__all_sync(kFull, mbar_try_wait(bar, parity))) {
-                            ++rctr;
-                            return true;
-                        }
-                    return false;
-                };
-                for (uint32_t i = 0; i < kStages; ++i) issue();
-                for (;;) {
-                    const uint64_t ws = ws0 + static_cast<uint64_t>(kWin) * j_read;
-                    const bool have = my_pending && s != dead && ws < stop;
-                    if (!__any_sync(kFull, have)) break;
-                    const uint32_t stage = rctr % kStages;
-                    if (!wait_stage()) {
-                        failed = true;
-                        break;
-                    }
-                    if (have) {
-                        const uint32_t sb = stg_base + (stage * 32 + lane) * kLaneStride;
-                        const uint64_t lo = max(pos, ws), hi = min(stop, ws + kWin);
-                        if (lo == ws && hi == ws + kWin) {
-#pragma unroll
-                            for (uint32_t g = 0; g < kWin / 16; ++g) {
-                                const uint4 v = lds_v4(sb + 16 * g);
-                                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-                                uint32_t cl[16];
-#pragma unroll
-                                for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
-#pragma unroll
-                                for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
-                            }
-                        } else {
-                            for (uint64_t q = lo; q < hi; ++q)
-                                s = T.next(s, T.cls_of(lds_u8(sb + static_cast<uint32_t>(q - ws))));
-                        }
-                        pos = hi;
-                    }
-                    ++j_read;
-                    __syncwarp();
-                    fence_proxy_async_smem();
-                    issue();
-                }
-                // windows issued past the last one read carry no bytes; consume their phases
-                while (!failed && rctr < wctr)
-                    if (!wait_stage()) failed = true;
-                if (failed) {
-                    // a copy did not land within the spin limit: report it, give the copies
-                    // still in flight one more bounded wait each, and leave
-                    if (lane == 0) atomicOr(p.status, kStatusTimeout);
-                    while (rctr < wctr) {
+                coop_converge<LUT, true>(T, stg_base, lane, my_pending, p.text, lim, min(end, lim), pos, s, dead);
+            }
+            if (PATH == kPathBulk) {
+                if (__any_sync(kFull, my_pending) && !failed) {
+                    // windows [ws0 + kWin*j, +kWin) of the 16-byte-aligned text; bytes at or past
+                    // `lim` (the text length rounded down to 16) are left to plain loads below
+                    const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
+                    const uint64_t ws0 = pos & ~static_cast<uint64_t>(15);
+                    const uint64_t stop = min(end, lim);
+                    uint32_t j_issue = 0, j_read = 0;
+                    auto issue = [&]() {
+                        const uint32_t stage = wctr % kStages;
+                        const uint32_t bar = bar_base + stage * 8;
+                        const uint64_t ws = ws0 + static_cast<uint64_t>(kWin) * j_issue;
+                        uint32_t bytes = 0;
+                        if (my_pending && s != dead && ws < stop)
+                            bytes = static_cast<uint32_t>(min(static_cast<uint64_t>(kWin), lim - ws));
+                        const uint32_t total = __reduce_add_sync(kFull, bytes);
+                        if (lane == 0) mbar_arrive_expect_tx(bar, total);
+                        __syncwarp();
+                        if (bytes)
+                            bulk_copy_g2s(stg_base + (stage * 32 + lane) * kLaneStride, p.text + ws, bytes, bar);
+                        ++wctr;
+                        ++j_issue;
+                    };
+                    auto wait_stage = [&]() -> bool {
                         const uint32_t bar = bar_base + (rctr % kStages) * 8;
                         const uint32_t parity = (rctr / kStages) & 1;
-                        for (uint32_t it = 0; it < kSpinLimit && !__all_sync(kFull, mbar_try_wait(bar, parity)); ++it) {
+                        for (uint32_t it = 0; it < kSpinLimit; ++it)
+                            if (__all_sync(kFull, mbar_try_wait(bar, parity))) {
+                                ++rctr;
+                                return true;
+                            }
+                        return false;
+                    };
+                    for (uint32_t i = 0; i < kStages; ++i) issue();
+                    for (;;) {
+                        const uint64_t ws = ws0 + static_cast<uint64_t>(kWin) * j_read;
+                        const bool have = my_pending && s != dead && ws < stop;
+                        if (!__any_sync(kFull, have)) break;
+                        const uint32_t stage = rctr % kStages;
+                        if (!wait_stage()) {
+                            failed = true;
+                            break;
                         }
-                        ++rctr;
+                        if (have) {
+                            const uint32_t sb = stg_base + (stage * 32 + lane) * kLaneStride;
+                            const uint64_t lo = max(pos, ws), hi = min(stop, ws + kWin);
+                            if (lo == ws && hi == ws + kWin) {
+#pragma unroll
+                                for (uint32_t g = 0; g < kWin / 16; ++g) s = run_granule(T, s, sb + 16 * g);
+                            } else {
+                                for (uint64_t q = lo; q < hi; ++q)
+                                    s = T.next(s, T.cls_of(lds_u8(sb + static_cast<uint32_t>(q - ws))));
+                            }
+                            pos = hi;
+                        }
+                        ++j_read;
+                        __syncwarp();
+                        fence_proxy_async_smem();
+                        issue();
                     }
-                    return;
+                    // windows issued past the last one read carry no bytes; consume their phases
+                    while (!failed && rctr < wctr)
+                        if (!wait_stage()) failed = true;
+                    if (failed) {
+                        // a copy did not land within the spin limit: report it, give the copies
+                        // still in flight one more bounded wait each, and leave
+                        if (lane == 0) atomicOr(p.status, kStatusTimeout);
+                        while (rctr < wctr) {
+                            const uint32_t bar = bar_base + (rctr % kStages) * 8;
+                            const uint32_t parity = (rctr / kStages) & 1;
+                            for (uint32_t it = 0; it < kSpinLimit && !__all_sync(kFull, mbar_try_wait(bar, parity)); ++it) {
+                            }
+                            ++rctr;
+                        }
+                        return;
+                    }
                 }
+            }
+            if (my_pending) {
+                tail_converge<LUT, PATH == kPathGlobal>(T, p.text, pos, end, s, dead);
+                if (total_runs > 32) wfin[idx] = s;
+                else fin_reg = s;
             }
         }
-        if (my_pending) {
-            const uint64_t ch = chunk0 + lane;
-            const uint8_t *t = p.text;
-            if (PATH == kPathGlobal) {
-                while (pos < end && (reinterpret_cast<uintptr_t>(t + pos) & 15)) {
-                    s = T.next(s, T.cls_of(__ldg(t + pos)));
-                    ++pos;
-                }
-                while (pos + 16 <= end && s != dead) {
-                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(t + pos));
-                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-                    uint32_t cl[16];
+        __syncwarp();
+        // ---------------- rows of the handed-off chunks, one chunk at a time by the warp
+        if (wball) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
+            for (int r = 0; r < R; ++r) amask[r] = wball[r * 32 + lane];
+        } else {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
-                    pos += 16;
-                }
-            }
-            while (pos < end && s != dead) {
-                s = T.next(s, T.cls_of(__ldg(t + pos)));
-                ++pos;
-            }
-            bool any = false;
+            for (int r = 0; r < R; ++r) amask[r] = 0xFFFFFFFFu;    // tags decide
+        }
+        for (uint32_t hm = handed; hm; hm &= hm - 1) {
+            const uint32_t j = __ffs(hm) - 1;
+            const uint32_t hand = __shfl_sync(kFull, my_hand, j);
+            const uint32_t m = hand >> 16, run0 = hand & 0xFFFF;
+            const uint32_t src = run0 + min(lane, m - 1);     // lane g < m: run of group g
+            uint32_t fin = __shfl_sync(kFull, fin_reg, src & 31);
+            if (total_runs > 32) fin = wfin[src];
+            uint32_t am = 0;
 #pragma unroll
-            for (int r = 0; r < R; ++r) any |= my_alive[r] != 0;
-            const uint32_t sid = T.id(s);
-            const uint16_t val = s == dead ? kUndef : static_cast<uint16_t>(sid);
-            write_row<R>(p.maps + ch * A.k, A.k, my_alive, val);
-            const bool live = any && s != dead;
-            p.dinfo[ch] = live ? ((1u << 16) | sid) : static_cast<uint32_t>(kUndef);
+            for (int r = 0; r < R; ++r) am |= ((amask[r] >> j) & 1u) << r;
+            finish_handed_row<R, LUT>(T, p.maps + (chunk0 + j) * A.k, A.k, m, m >= 2 || !wball, lane, am, fin,
+                                      dead, p.dinfo + chunk0 + j);
         }
     }
 }
@@ -595,93 +321,9 @@ __device__ __forceinline__ bool speculate_chunk(const ReachArgs &p, const LUT &T
                                                 uint32_t lane, const uint32_t (&start_state)[R],
                                                 uint32_t start_live, uint32_t dead, uint64_t *out_pos,
                                                 uint32_t *out_state, uint32_t (&alive)[R]) {
-    const Automaton &A = p.A;
-    const uint64_t beg = chunk_begin(ch, p.len, p.c);
-    const uint64_t end = chunk_begin(ch + 1, p.len, p.c);
-    uint32_t s[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) s[r] = start_state[r];
-    uint32_t live_regs = start_live;
-    uint64_t pos = beg;
-    bool converged = false;
-    uint32_t conv_state = dead;
-    while (pos < end) {
-        const uint64_t stop = min(end, pos + p.probe);
-        for (; pos < stop; ++pos) {
-            const uint32_t c = T.cls_of(__ldg(p.text + pos));
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (live_regs & (1u << r)) s[r] = T.next(s[r], c);
-        }
-        uint32_t lo = 0xFFFFFFFFu, hi = 0;
-        live_regs = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (__any_sync(kFull, s[r] != dead)) live_regs |= 1u << r;
-            if (s[r] != dead) {
-                lo = min(lo, s[r]);
-                hi = max(hi, s[r]);
-            }
-        }
-        lo = __reduce_min_sync(kFull, lo);
-        hi = __reduce_max_sync(kFull, hi);
-        if (lo == 0xFFFFFFFFu || lo == hi) {
-            converged = true;
-            conv_state = (lo == 0xFFFFFFFFu) ? dead : lo;
-            break;
-        }
-    }
-    if (converged && pos < end && conv_state != dead) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) alive[r] = __ballot_sync(kFull, s[r] != dead);
-        *out_pos = pos;
-        *out_state = conv_state;
-        return true;
-    }
-    uint16_t *row = p.maps + ch * A.k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t a = r * 32 + lane;
-        if (a < A.k) row[a] = s[r] == dead ? kUndef : static_cast<uint16_t>(T.id(s[r]));
-    }
-    uint32_t cnt = 0, first = kUndef, cur = 0;
-    bool more = true;
-    while (more) {
-        uint32_t v = 0xFFFFFFFFu;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-            if (s[r] != dead && (cnt == 0 || s[r] > cur)) v = min(v, s[r]);
-        v = __reduce_min_sync(kFull, v);
-        if (v == 0xFFFFFFFFu) {
-            more = false;
-        } else {
-            if (cnt == 0) first = T.id(v);
-            cur = v;
-            if (++cnt > kMaxD) more = false;
-        }
-    }
-    if (lane == 0) {
-        if (cnt > kMaxD) {
-            p.dinfo[ch] = (0xFFu << 16) | first;
-            atomicOr(p.status, kStatusWide);
-        } else {
-            p.dinfo[ch] = (cnt << 16) | first;
-        }
-    }
-    return false;
-}
-
-// 16 transitions of one chain over one 16-byte granule held in shared memory.
-template <class LUT>
-__device__ __forceinline__ uint32_t run_granule(const LUT &T, uint32_t s, uint32_t addr) {
-    const uint4 x = lds_v4(addr);
-    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-    uint32_t cl[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
-    return s;
+    return speculate_range<R, LUT>(T, p.A, p.text, chunk_begin(ch, p.len, p.c), chunk_begin(ch + 1, p.len, p.c),
+                                   p.probe, lane, start_state, start_live, dead, p.maps + ch * p.A.k,
+                                   p.dinfo + ch, p.status, out_pos, out_state, alive);
 }
 
 // The same for two independent chains, interleaved so their lookups overlap.
@@ -1102,46 +744,11 @@ __global__ void __launch_bounds__(kJoinThreads) rid_join_kernel(JoinArgs p) {
     *p.accept = acc;
 }
 
-// --------------------------------------------------------------------------- host side
-inline int cuda_fail(cudaError_t e) {
-    (void)cudaGetLastError();
-    return e == cudaErrorMemoryAllocation ? RIDFA_E_NOMEM : RIDFA_E_CUDA;
-}
-
-int upload(const HostAutomaton &H, DeviceAutomaton &D, int dev) {
-    D.device = dev;
-    const size_t bt = H.trans.size() * 2, bf = H.final_bits.size() * 4, bi = H.ifmask.size() * 4,
-                 bs = H.slot_state.size() * 2;
-    auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
-    const size_t total = al(bt) + al(256) + al(bf) + al(bi) + al(bs);
-    uint8_t *base = nullptr;
-    cudaError_t e = cudaMalloc(&base, total);
-    if (e != cudaSuccess) return cuda_fail(e);
-    size_t off = 0;
-    D.trans = reinterpret_cast<uint16_t *>(base + off); off += al(bt);
-    D.classmap = base + off; off += al(256);
-    D.final_bits = reinterpret_cast<uint32_t *>(base + off); off += al(bf);
-    D.ifmask = reinterpret_cast<uint32_t *>(base + off); off += al(bi);
-    D.slot_state = reinterpret_cast<uint16_t *>(base + off); off += al(bs);
-    D.bytes = total;
-    e = cudaMemcpy(D.trans, H.trans.data(), bt, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(D.classmap, H.classmap.data(), 256, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && bf) e = cudaMemcpy(D.final_bits, H.final_bits.data(), bf, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && bi) e = cudaMemcpy(D.ifmask, H.ifmask.data(), bi, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && bs) e = cudaMemcpy(D.slot_state, H.slot_state.data(), bs, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        cudaFree(base);
-        D = DeviceAutomaton{};
-        return cuda_fail(e);
-    }
-    return RIDFA_OK;
-}
-
 struct Layout {   // scratch layout for one call
-    size_t maps_off, dinfo_off, partials_off, ticket_off, status_off, accept_off, total;
+    size_t maps_off, dinfo_off, partials_off, ticket_off, status_off, accept_off, runs_off, finals_off, total;
 };
 
-Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks) {
+Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks, uint64_t grid_warps) {
     auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
     Layout L{};
     size_t off = 0;
@@ -1150,6 +757,8 @@ Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks) 
     L.accept_off = off; off += 256;
     L.partials_off = off; off += al(static_cast<size_t>(join_blocks) * (1 + kMaxD) * 4);
     L.dinfo_off = off; off += al(c * 4);
+    L.runs_off = off; off += al(grid_warps * kRunsPerWarp * sizeof(RunEntry));
+    L.finals_off = off; off += al(grid_warps * kFinalsPerWarp * 4);
     L.maps_off = off; off += need_maps ? al(c * k * 2) : 0;
     L.total = off;
     return L;
@@ -1182,24 +791,6 @@ DeviceScratch *scratch_for(const ridfa_program *P, int dev, size_t bytes, int *e
         S->bytes = want;
     }
     return S;
-}
-
-const DeviceAutomaton *device_copy(const ridfa_program *P, bool dfa, int dev, int *err) {
-    auto &vec = dfa ? P->dev_dfa : P->dev_rid;
-    for (auto &d : vec)
-        if (d.device == dev) return &d;
-    DeviceAutomaton D;
-    *err = upload(dfa ? P->dfa : P->rid, D, dev);
-    if (*err != RIDFA_OK) return nullptr;
-    vec.push_back(D);
-    return &vec.back();
-}
-
-int smem_optin_limit() {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return v;
 }
 
 enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3 };
@@ -1383,7 +974,18 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     uint32_t join_blocks = static_cast<uint32_t>(std::max<uint64_t>(
         1, (nbound + static_cast<uint64_t>(kJoinThreads) * per_thread - 1) /
                (static_cast<uint64_t>(kJoinThreads) * per_thread)));
-    const Layout L = layout_for(c, H.k, d_maps_user == nullptr, join_blocks);
+    Automaton A{D->trans, D->classmap, D->final_bits, D->ifmask, D->slot_state,
+                H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+    // plan the reach launch first: the run-list scratch is sized by its grid
+    ReachArgs ra{A, d_text, len, n_chunks, nullptr, nullptr, nullptr, 8, nullptr, nullptr};
+    if (tuning && tuning->probe_interval) ra.probe = tuning->probe_interval;
+    ReachPlan plan;
+    err = plan_reach(A, tuning, d_text, ra, sms, &plan);
+    if (err != RIDFA_OK) return err;
+    // warps past the last 32-chunk task never write their run list
+    const uint64_t grid_warps = std::min<uint64_t>(static_cast<uint64_t>(plan.grid) * (plan.block / 32),
+                                                   (n_chunks + 31) / 32);
+    const Layout L = layout_for(c, H.k, d_maps_user == nullptr, join_blocks, grid_warps);
     DeviceScratch *S = scratch_for(P, dev, L.total, &err);
     if (!S) return err;
     uint8_t *base = static_cast<uint8_t *>(S->base);
@@ -1393,18 +995,14 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     uint16_t *maps = d_maps_user ? d_maps_user : reinterpret_cast<uint16_t *>(base + L.maps_off);
     uint32_t *dinfo = reinterpret_cast<uint32_t *>(base + L.dinfo_off);
     uint32_t *partials = reinterpret_cast<uint32_t *>(base + L.partials_off);
-
-    Automaton A{D->trans, D->classmap, D->final_bits, D->ifmask, D->slot_state,
-                H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+    ra.maps = maps;
+    ra.dinfo = dinfo;
+    ra.status = status;
+    ra.runs = reinterpret_cast<RunEntry *>(base + L.runs_off);
+    ra.finals = reinterpret_cast<uint32_t *>(base + L.finals_off);
     e = cudaMemsetAsync(status, 0, 4, st);
     if (e != cudaSuccess) return cuda_fail(e);
 
-    // ---- reach
-    ReachArgs ra{A, d_text, len, n_chunks, maps, dinfo, status, 8};
-    if (tuning && tuning->probe_interval) ra.probe = tuning->probe_interval;
-    ReachPlan plan;
-    err = plan_reach(A, tuning, d_text, ra, sms, &plan);
-    if (err != RIDFA_OK) return err;
     const bool prof = tuning && tuning->profile;
     if (prof) {
         for (auto &ev : S->ev)
@@ -1484,7 +1082,7 @@ int launch_with_buffers(const HostAutomaton &H, const PreparedBuffers &B, const 
         1, (nbound + kJoinThreads * per_thread - 1) / (kJoinThreads * per_thread)));
     Automaton A{B.trans, B.classmap, B.final_bits, B.ifmask, B.slot_state,
                 H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
-    ReachArgs ra{A, d_text, len, n_chunks, B.maps, B.dinfo, B.status, 8};
+    ReachArgs ra{A, d_text, len, n_chunks, B.maps, B.dinfo, B.status, 8, nullptr, nullptr};
     ReachPlan plan;
     int err = plan_reach(A, nullptr, d_text, ra, sms, &plan);
     if (err != RIDFA_OK) return err;

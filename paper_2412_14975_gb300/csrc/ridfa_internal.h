@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cstddef>
+#include <cuda_runtime_api.h>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -86,6 +87,12 @@ struct PreparedBuffers {
     uint32_t *status;      // zero before the launch
     uint8_t *accept;
 };
+// Host helpers of the device code (ridfa_device.cu), shared with the batched path.
+int cuda_fail(cudaError_t e);
+int upload(const HostAutomaton &H, DeviceAutomaton &D, int dev);
+const DeviceAutomaton *device_copy(const ridfa_program *P, bool dfa, int dev, int *err);
+int smem_optin_limit();
+
 constexpr uint32_t kMaxJoinBlocks = 1024;
 constexpr uint32_t kPartialWords = 33;
 

@@ -1,0 +1,558 @@
+// Device building blocks shared by the single-text kernels (ridfa_device.cu) and the batched
+// kernels (ridfa_batch.cu): constants, the device view of an automaton, shared-memory and
+// asynchronous-copy helpers, the table lookup policies, and the speculative phase of one chunk.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ridfa_internal.h"
+
+namespace ridfa {
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint16_t kUndef = 0xFFFF;
+constexpr uint32_t kStatusWide = 1u;      // some chunk has > 32 distinct end states
+constexpr uint32_t kStatusBad = 2u;       // a device consistency check failed
+constexpr int kMaxD = 32;                 // distinct end states handled by the matrix join
+constexpr int kJoinThreads = 256;
+static_assert(kPartialWords == 1 + kMaxD, "join partial layout");
+
+struct Automaton {            // device view of one automaton
+    const uint16_t *trans;    // [(n+1) * C]
+    const uint8_t *classmap;  // [256]
+    const uint32_t *final_bits;
+    const uint32_t *ifmask;   // [(n+1) * kw]
+    const uint16_t *slot_state;
+    uint32_t n, C, k, kw, q0_slot;
+};
+
+__host__ __device__ inline uint64_t chunk_begin(uint64_t i, uint64_t len, uint64_t c) {
+    // floor(i * len / c) without 128-bit products: i*(len/c) + (i*(len%c))/c
+    return i * (len / c) + (i * (len % c)) / c;
+}
+
+// ------------------------------------------------------------------------------ reach
+// A run handed from the speculative phase to one lane: chunk j of the warp's task, resume
+// position, state (policy encoding), and the group of slots that share it.
+struct RunEntry {
+    uint64_t pos;
+    uint32_t state;
+    uint16_t chunk;
+    uint16_t group;
+};
+constexpr int kMaxRun = 8;              // distinct live states one chunk may hand off
+constexpr uint32_t kMultiMin = 64;      // speculated bytes before a multi-run hand-off is tried
+constexpr uint32_t kRunsPerWarp = 32 * kMaxRun;
+// per-warp words of the finals area: the final state of each run, then the alive bits of the
+// task's hand-offs (word 32*r + lane: bit j = slot 32*r + lane alive at chunk j's hand-off)
+constexpr uint32_t kFinalsPerWarp = kRunsPerWarp + 32 * 8;
+static_assert(kMaxRun <= 8, "group tags keep the group in the low 3 bits");
+
+struct ReachArgs {
+    Automaton A;
+    const uint8_t *text;
+    uint64_t len;
+    uint32_t c;
+    uint16_t *maps;           // [c][k]
+    uint32_t *dinfo;          // [c]: (m << 16) | min defined end state (0xFFFF if none)
+    uint32_t *status;
+    uint32_t probe;
+    RunEntry *runs;           // [grid warps][kRunsPerWarp], or null: only single-run hand-offs
+    uint32_t *finals;         // [grid warps][kFinalsPerWarp]
+};
+
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Text staging for the converged phase (TMA path): every lane streams its own chunk through a
+// ring of kStages windows of kWin bytes in shared memory, filled by 1-D bulk copies
+// (cp.async.bulk) that complete on one mbarrier per warp and stage.  A lane's window buffers
+// are kLaneStride bytes apart, so the 16-byte reads of 8 consecutive lanes fall in 8 different
+// bank groups (stride 48 = 3 granules, and 3 is odd).
+constexpr uint32_t kWin = 128;
+constexpr uint32_t kStages = 2;
+constexpr uint32_t kLaneStride = 144;
+// per-warp ring + barriers, rounded to 16 bytes so every warp's ring starts 16-byte aligned
+// (bulk-copy destinations must be)
+constexpr uint32_t kWarpStageBytes = (kStages * 32 * kLaneStride + kStages * 8 + 15) & ~15u;
+static_assert(kWarpStageBytes % 16 == 0 && (kStages * 32 * kLaneStride) % 16 == 0 && kLaneStride % 16 == 0,
+              "bulk-copy destinations must stay 16-byte aligned");
+constexpr uint32_t kStatusTimeout = 4u;   // a bounded wait on a copy gave up
+// text paths of the converged phase
+constexpr int kPathGlobal = 0;   // each lane: 16-byte global loads of its own chunk
+constexpr int kPathBulk = 1;     // each lane: 1-D bulk copies into a shared-memory ring
+constexpr int kPathCoop = 2;     // the warp: coalesced loads of 8 chunks' windows per instruction
+constexpr int kPathCoop2 = 3;    // the same with two chunks per lane, interleaved
+// cooperative path: one 64-byte window per chunk of the warp; granule g of chunk j's window sits
+// at 16-byte unit 4j + (g ^ ((j >> 1) & 3)), so both the stores (lanes write 4 granules of 2
+// chunks per 8-lane phase) and the owners' 16-byte reads (8 chunks, one granule each) are
+// conflict-free
+constexpr uint32_t kCoopWin = 64;
+constexpr uint32_t kCoopBufBytes = 32 * kCoopWin;          // one round: a window per chunk
+constexpr uint32_t kWarpCoopBytes = 2 * kCoopBufBytes;     // double-buffered
+
+__device__ __forceinline__ void cp_async_16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ uint32_t coop_unit(uint32_t j, uint32_t g) { return 4 * j + (g ^ ((j >> 1) & 3)); }
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t tx) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P1;\n\t}"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ uint4 lds_v4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u8(uint32_t addr) {
+    uint16_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v;
+}
+
+// Table lookup policies.  A run's state is kept in the policy's own encoding (`enc`); `id`
+// recovers the automaton state number.
+//
+// Plain: compact uint16 table [(n+1) * C] and uint8 class map, in shared memory (or global
+// memory when it does not fit).  Lanes gathering different entries may hit the same bank.
+struct LutPlain {
+    const uint16_t *t;
+    const uint8_t *cls;
+    uint32_t C;
+    static size_t smem_bytes(const Automaton &A) { return 256 + static_cast<size_t>(A.n + 1) * A.C * 2; }
+    __device__ void setup(const Automaton &A, uint8_t *smem, bool table_in_smem) {
+        uint8_t *s_cls = smem;
+        uint16_t *s_t = reinterpret_cast<uint16_t *>(smem + 256);
+        for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_cls[i] = A.classmap[i];
+        if (table_in_smem)
+            for (uint32_t i = threadIdx.x; i < (A.n + 1) * A.C; i += blockDim.x) s_t[i] = A.trans[i];
+        t = table_in_smem ? s_t : A.trans;
+        cls = s_cls;
+        C = A.C;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id; }
+    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s; }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return cls[b]; }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return t[s * C + c]; }
+};
+
+// Lane-replicated tables: every entry is stored 32 times, lane l's copy in bank l, so a warp's
+// 32 gathers are always one shared-memory wavefront whatever states and bytes the lanes hold.
+// Entries hold byte offsets, so a step is one add and one load:
+//   class table, 32-bit words: word (b * 32 + l) = class offset of byte b;
+//   Rep16 transition table, 16-bit halves: entry (s, c) at byte
+//       (s * Cp/2 + c/2) * 128 + l * 4 + (c & 1) * 2,   value = state offset s' * Cp * 64;
+//   Rep32 transition table, 32-bit words: entry (s, c) at word (s * C + c) * 32 + l,
+//       value = s' * C * 128.
+template <bool W16>
+struct LutRep {
+    uint32_t lc, lt;          // shared addresses of this lane's class / transition copies
+    uint32_t row;             // state offset stride
+    __host__ __device__ static uint32_t cpad(const Automaton &A) { return W16 ? (A.C + 1) & ~1u : A.C; }
+    static size_t smem_bytes(const Automaton &A) {
+        return 256 * 128 + static_cast<size_t>(A.n + 1) * cpad(A) * (W16 ? 64 : 128);
+    }
+    static bool fits16(const Automaton &A) {
+        return static_cast<uint64_t>(A.n) * cpad(A) * 64 + 128 * ((cpad(A) - 1) / 2) + 2 <= 0xFFFF;
+    }
+    __device__ __forceinline__ uint32_t cls_off(uint32_t c) const {
+        return W16 ? (c >> 1) * 128 + (c & 1) * 2 : c * 128;
+    }
+    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+        const uint32_t Cp = cpad(A);
+        row = W16 ? Cp * 64 : Cp * 128;
+        const uint32_t base_c = smem_addr(smem);
+        const uint32_t base_t = base_c + 256 * 128;
+        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x)
+            sts_u32(base_c + i * 4, cls_off(A.classmap[i >> 5]));
+        const uint32_t words = W16 ? (A.n + 1) * Cp / 2 : (A.n + 1) * Cp;
+        for (uint32_t i = threadIdx.x; i < words * 32; i += blockDim.x) {
+            const uint32_t w = i >> 5;
+            uint32_t v;
+            if (W16) {
+                const uint32_t s = (2 * w) / Cp, c0 = (2 * w) % Cp;
+                const uint32_t n0 = A.trans[s * A.C + c0];
+                const uint32_t n1 = (c0 + 1 < A.C) ? A.trans[s * A.C + c0 + 1] : A.n;
+                v = (n0 * row) | ((n1 * row) << 16);
+            } else {
+                v = A.trans[w] * row;
+            }
+            sts_u32(base_t + i * 4, v);
+        }
+        const uint32_t lane = threadIdx.x & 31;
+        lc = base_c + lane * 4;
+        lt = base_t + lane * 4;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id * row; }
+    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s / row; }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const {
+        return W16 ? lds_u16(lt + s + c) : lds_u32(lt + s + c);
+    }
+};
+
+// Chunk-map row of one chunk written by one lane: entries of alive slots get `val`.
+template <int R>
+__device__ __forceinline__ void write_row(uint16_t *row, uint32_t k, const uint32_t (&alive)[R],
+                                          uint16_t val) {
+    if ((k & 1) == 0) {
+        uint32_t *row32 = reinterpret_cast<uint32_t *>(row);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t m = alive[r];
+            for (uint32_t l = 0; l < 32; l += 2) {
+                const uint32_t a = r * 32 + l;
+                if (a >= k) break;
+                const uint32_t lo = ((m >> l) & 1) ? val : kUndef;
+                const uint32_t hi = ((m >> (l + 1)) & 1) ? val : kUndef;
+                row32[a >> 1] = lo | (hi << 16);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t m = alive[r];
+            for (uint32_t l = 0; l < 32; ++l) {
+                const uint32_t a = r * 32 + l;
+                if (a >= k) break;
+                row[a] = ((m >> l) & 1) ? val : kUndef;
+            }
+        }
+    }
+}
+
+
+// Speculative phase of one chunk text[beg, end) by the whole warp (lanes = runs; slot
+// a = 32*r + lane in register r).  Every `probe` bytes the warp drops registers whose runs are all
+// dead and checks whether the live runs sit in one state (redux.sync min == max).  With `multi`
+// set, once kMultiMin bytes have been speculated it also hands off as soon as the live runs sit in
+// at most kMaxRun distinct states, each as a run of its own.
+//
+// Return m >= 1 (handed off before `end`): *out_pos is the resume position, lane g < m holds the
+// g-th distinct live state (ascending) in *my_d (for m = 1 every lane holds it), alive[] holds
+// the ballots of the slots still alive (the same in every lane), and for m >= 2 (or any m when
+// `tag_all`) the chunk's map row holds a group tag per alive slot (0x8000 | g) and 0xFFFF for a
+// dead one, to be replaced once the runs end.
+// Return 0: the chunk finished here; its map row (`row`, k entries) and its D_i summary
+// (`*dinfo_slot`) are written.
+template <int R, class LUT>
+__device__ __forceinline__ int speculate(const LUT &T, const Automaton &A, const uint8_t *text,
+                                         uint64_t beg, uint64_t end, uint32_t probe, uint32_t lane,
+                                         const uint32_t (&start_state)[R], uint32_t start_live,
+                                         uint32_t dead, uint16_t *row, uint32_t *dinfo_slot,
+                                         uint32_t *status, bool multi, bool tag_all, uint64_t *out_pos,
+                                         uint32_t *my_d, uint32_t (&alive)[R]) {
+    uint32_t s[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) s[r] = start_state[r];
+    uint32_t live_regs = start_live;
+    uint64_t pos = beg;
+    int m = 0;
+    uint32_t d = dead;
+    while (pos < end) {
+        const uint64_t stop = min(end, pos + probe);
+        for (; pos < stop; ++pos) {
+            const uint32_t c = T.cls_of(__ldg(text + pos));
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (live_regs & (1u << r)) s[r] = T.next(s[r], c);
+        }
+        uint32_t lo = 0xFFFFFFFFu, hi = 0;
+        live_regs = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (__any_sync(kFull, s[r] != dead)) live_regs |= 1u << r;
+            if (s[r] != dead) {
+                lo = min(lo, s[r]);
+                hi = max(hi, s[r]);
+            }
+        }
+        lo = __reduce_min_sync(kFull, lo);
+        hi = __reduce_max_sync(kFull, hi);
+        if (lo == 0xFFFFFFFFu) break;                     // every run died: finish here
+        if (lo == hi) {
+            if (pos < end) {
+                m = 1;
+                d = lo;
+            }
+            break;
+        }
+        if (multi && pos < end && pos - beg >= kMultiMin) {
+            // the distinct live states in ascending order, lane g taking the g-th, while there
+            // are at most kMaxRun of them
+            uint32_t cnt = 0, cur = 0, mine = dead;
+            for (;;) {
+                uint32_t v = 0xFFFFFFFFu;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (s[r] != dead && (cnt == 0 || s[r] > cur)) v = min(v, s[r]);
+                v = __reduce_min_sync(kFull, v);
+                if (v == 0xFFFFFFFFu) break;
+                if (cnt == static_cast<uint32_t>(kMaxRun)) {
+                    cnt = kMaxRun + 1;
+                    break;
+                }
+                if (lane == cnt) mine = v;
+                cur = v;
+                ++cnt;
+            }
+            if (cnt <= static_cast<uint32_t>(kMaxRun)) {
+                m = static_cast<int>(cnt);
+                d = mine;
+                break;
+            }
+        }
+    }
+    if (m >= 1) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) alive[r] = __ballot_sync(kFull, s[r] != dead);
+        if (m >= 2 || tag_all) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                uint32_t tag = kUndef;
+                for (int g = 0; g < m; ++g) {
+                    const uint32_t dg = __shfl_sync(kFull, d, g);     // every lane takes part
+                    if (s[r] != dead && dg == s[r]) tag = 0x8000u | g;
+                }
+                const uint32_t a = r * 32 + lane;
+                if (a < A.k) row[a] = static_cast<uint16_t>(tag);
+            }
+        }
+        *out_pos = pos;
+        *my_d = d;
+        return m;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t a = r * 32 + lane;
+        if (a < A.k) row[a] = s[r] == dead ? kUndef : static_cast<uint16_t>(T.id(s[r]));
+    }
+    uint32_t cnt = 0, first = kUndef, cur = 0;
+    bool more = true;
+    while (more) {
+        uint32_t v = 0xFFFFFFFFu;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (s[r] != dead && (cnt == 0 || s[r] > cur)) v = min(v, s[r]);
+        v = __reduce_min_sync(kFull, v);
+        if (v == 0xFFFFFFFFu) {
+            more = false;
+        } else {
+            if (cnt == 0) first = T.id(v);
+            cur = v;
+            if (++cnt > kMaxD) more = false;
+        }
+    }
+    if (lane == 0) {
+        if (cnt > kMaxD) {
+            *dinfo_slot = (0xFFu << 16) | first;
+            atomicOr(status, kStatusWide);
+        } else {
+            *dinfo_slot = (cnt << 16) | first;
+        }
+    }
+    return 0;
+}
+
+// The single-run form: true when the live runs merged into one state before `end`
+// (*out_state), false when the chunk finished in the speculative phase.
+template <int R, class LUT>
+__device__ __forceinline__ bool speculate_range(const LUT &T, const Automaton &A, const uint8_t *text,
+                                                uint64_t beg, uint64_t end, uint32_t probe,
+                                                uint32_t lane, const uint32_t (&start_state)[R],
+                                                uint32_t start_live, uint32_t dead, uint16_t *row,
+                                                uint32_t *dinfo_slot, uint32_t *status,
+                                                uint64_t *out_pos, uint32_t *out_state,
+                                                uint32_t (&alive)[R]) {
+    return speculate<R, LUT>(T, A, text, beg, end, probe, lane, start_state, start_live, dead, row,
+                             dinfo_slot, status, false, false, out_pos, out_state, alive) == 1;
+}
+
+// Map row and D_i summary of a handed-off chunk, by the whole warp, once its runs have ended.
+// `am` is this lane's alive bit of each of its slots (bit r: slot 32*r + lane); lane g < m holds
+// the final state of group g in `fin`.  Untagged rows (m = 1 without tag_all) are written from
+// the alive bits alone; tagged rows are read back and their group tags replaced.
+template <int R, class LUT>
+__device__ __forceinline__ void finish_handed_row(const LUT &T, uint16_t *row, uint32_t k, uint32_t m,
+                                                  bool tagged, uint32_t lane, uint32_t am, uint32_t fin,
+                                                  uint32_t dead, uint32_t *dinfo_slot) {
+    const uint32_t fid = (lane < m && fin != dead) ? T.id(fin) : kUndef;
+    if (!tagged) {
+        const uint32_t v = __shfl_sync(kFull, fid, 0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t a = r * 32 + lane;
+            if (a < k) row[a] = static_cast<uint16_t>(((am >> r) & 1) ? v : kUndef);
+        }
+        if (lane == 0) *dinfo_slot = v == kUndef ? static_cast<uint32_t>(kUndef) : ((1u << 16) | v);
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t a = r * 32 + lane;
+        const uint32_t t = (a < k && ((am >> r) & 1)) ? row[a] : kUndef;
+        const bool live = t != kUndef;
+        const uint32_t v = __shfl_sync(kFull, fid, live ? (t & 7) : 0);
+        if (a < k) row[a] = static_cast<uint16_t>(live ? v : kUndef);
+    }
+    // every group owns at least one slot: D_i is the set of defined group finals
+    bool dup = false;
+    for (uint32_t h = 0; h < m; ++h) {
+        const uint32_t fh = __shfl_sync(kFull, fid, h);
+        if (h < lane && fh == fid) dup = true;
+    }
+    const bool uniq = lane < m && fid != kUndef && !dup;
+    const uint32_t cnt = __popc(__ballot_sync(kFull, uniq));
+    const uint32_t first = __reduce_min_sync(kFull, uniq ? fid : static_cast<uint32_t>(kUndef));
+    if (lane == 0) *dinfo_slot = cnt ? ((cnt << 16) | first) : static_cast<uint32_t>(kUndef);
+}
+
+// 16 transitions of one run over one 16-byte granule held in shared memory.
+template <class LUT>
+__device__ __forceinline__ uint32_t run_granule(const LUT &T, uint32_t s, uint32_t addr) {
+    const uint4 x = lds_v4(addr);
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+    uint32_t cl[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
+    return s;
+}
+
+// Converged phase of up to 32 runs, one per lane, with the text staged by the warp.  Lane l's
+// run (if `pending`) advances from `pos` to `stop` over its own text `base`; `lim` is that
+// text's length rounded down to 16 (the same for every lane when ONE_TEXT), and stop <= lim:
+// what lies past `lim` is left to the caller's plain loads.  The windows [wb + 64r, +64) of
+// each run (wb = the 16-byte boundary at or below `pos`) are copied with cp.async (L2 to shared
+// memory, no register or L1 round trip): lane l copies granule (l & 3) of the windows of runs
+// (l >> 2) + 8u, u = 0..3, so one instruction moves 8 runs' windows; one round ahead,
+// double-buffered, in the XOR-swizzled layout of coop_unit.
+template <class LUT, bool ONE_TEXT>
+__device__ __forceinline__ void coop_converge(const LUT &T, uint32_t stg_base, uint32_t lane, bool pending,
+                                              const uint8_t *base, uint64_t lim, uint64_t stop,
+                                              uint64_t &pos, uint32_t &s, uint32_t dead) {
+    const uint64_t wb = pos & ~static_cast<uint64_t>(15);
+    const uint32_t nwin = (pending && wb < stop)
+                              ? static_cast<uint32_t>((stop - wb + kCoopWin - 1) / kCoopWin) : 0;
+    const uint64_t waddr = reinterpret_cast<uint64_t>(base) + wb;
+    const uint64_t wlim = reinterpret_cast<uint64_t>(base) + lim;
+    const uint32_t g = lane & 3;
+    const uint32_t max_win = __reduce_max_sync(kFull, nwin);
+    auto issue = [&](uint32_t r) {
+        const uint32_t buf = stg_base + (r & 1) * kCoopBufBytes;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = u * 8 + (lane >> 2);        // run whose granule g this lane copies
+            const uint64_t a = __shfl_sync(kFull, waddr, j) + static_cast<uint64_t>(kCoopWin) * r + 16 * g;
+            const uint32_t nw = __shfl_sync(kFull, nwin, j);
+            const uint64_t la = ONE_TEXT ? wlim : __shfl_sync(kFull, wlim, j);
+            if (r < nw && a + 16 <= la) cp_async_16(buf + 16 * coop_unit(j, g), reinterpret_cast<const void *>(a));
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    const uint32_t sw = (lane >> 1) & 3;
+    for (uint32_t r = 0; r < max_win; ++r) {
+        if (r + 1 < max_win) issue(r + 1);
+        else cp_async_commit();               // keep one group per round
+        cp_async_wait1();                     // this lane's copies of round r have landed
+        __syncwarp();                         // ... and every other lane's
+        const uint64_t ws = wb + static_cast<uint64_t>(kCoopWin) * r;
+        if (r < nwin && s != dead) {
+            const uint32_t sb = stg_base + (r & 1) * kCoopBufBytes + 64 * lane;
+            const uint64_t lo = max(pos, ws), hi = min(stop, ws + kCoopWin);
+            if (lo == ws && hi == ws + kCoopWin) {
+#pragma unroll
+                for (uint32_t q16 = 0; q16 < kCoopWin / 16; ++q16) s = run_granule(T, s, sb + 16 * (q16 ^ sw));
+            } else {
+                for (uint64_t q = lo; q < hi; ++q) {
+                    const uint32_t o = static_cast<uint32_t>(q - ws);
+                    s = T.next(s, T.cls_of(lds_u8(sb + 16 * ((o >> 4) ^ sw) + (o & 15))));
+                }
+            }
+            pos = hi;
+        }
+        __syncwarp();                         // buffer (r & 1) is refilled next round
+    }
+    cp_async_wait0();
+    __syncwarp();
+}
+
+// The rest of one run, text[pos, end), with plain global loads (16-byte vector loads once
+// aligned when VEC).
+template <class LUT, bool VEC>
+__device__ __forceinline__ void tail_converge(const LUT &T, const uint8_t *t, uint64_t &pos, uint64_t end,
+                                              uint32_t &s, uint32_t dead) {
+    if (VEC) {
+        while (pos < end && (reinterpret_cast<uintptr_t>(t + pos) & 15)) {
+            s = T.next(s, T.cls_of(__ldg(t + pos)));
+            ++pos;
+        }
+        while (pos + 16 <= end && s != dead) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(t + pos));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            uint32_t cl[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
+            pos += 16;
+        }
+    }
+    while (pos < end && s != dead) {
+        s = T.next(s, T.cls_of(__ldg(t + pos)));
+        ++pos;
+    }
+}
+
+__device__ __forceinline__ bool is_final_state(const Automaton &A, uint32_t s) {
+    return s < A.n && ((A.final_bits[s >> 5] >> (s & 31)) & 1);
+}
+
+}  // namespace
+}  // namespace ridfa

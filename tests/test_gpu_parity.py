@@ -153,6 +153,19 @@ def test_many_distinct_end_states(nb):
     check(re_src, y, 100, dfa_too=False)
 
 
+def test_multi_run_handoff_rows():
+    """Chunks whose live runs never merge into one state (the {2,4} codon RE keeps up to five
+    distinct states) are handed off as several runs each; with ~1 KiB chunks a warp holds over 32
+    runs, so the finals go through the run list.  Every row, ragged last chunk included."""
+    re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
+    x = textgen.c2_text((1 << 20) + 13, seed=91)
+    for c in (1000, 3001):
+        for path in (1, 2, 3):
+            check(re2, x, c, dfa_too=False, rows=list(range(c)), tuning=dict(text_path=path))
+    y, _ = textgen.mutate(x, seed=92, n_subs=3, alphabet=b"ACGT")
+    check(re2, y, 1000, dfa_too=False, rows=list(range(1000)))
+
+
 @pytest.mark.parametrize("path", [1, 2, 3, 4])
 def test_text_paths_agree(path):
     """16-byte global loads and bulk-copy staging give the same maps, on aligned texts and on

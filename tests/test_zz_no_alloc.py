@@ -36,8 +36,10 @@ def test_noalloc_matches_recognize_twice_in_a_row():
     x3 = textgen.c3_text(1 << 20, seed=21)
     x3m, _ = textgen.mutate(x3, seed=22, n_subs=2)
     x1 = textgen.c1_text(1 << 18, seed=23)
+    x2 = textgen.c2_text(1 << 18, seed=24)     # runs that never merge: single-run hand-offs only
+    re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
     for re_src, text, c in [(textgen.C3_RE, x3, 1000), (textgen.C3_RE, x3m, 4096),
-                            (textgen.C1_RE, x1, 64), (textgen.C1_RE, x1, 7)]:
+                            (textgen.C1_RE, x1, 64), (textgen.C1_RE, x1, 7), (re2, x2, 300)]:
         cases.append((lib.ridfa_compile(re_src), torch.from_numpy(text.copy()).to("cuda:0"),
                       text.size, c))
     # alternate programs so each call has to bring its own tables into the shared array
