@@ -154,10 +154,67 @@ def cpu_baseline(name, re_src, budget_s=12.0, seed=7):
                       f"state-set simulation pass ({dt:.1f} s)"}
 
 
+def run_reference_multi(args, name):
+    """The oracle on the batched or served workload: a bounded sample of its texts, item by item.
+    (The workload's random REs are selected with the library's host compiler; the timed path is
+    the oracle alone.)"""
+    import numpy as np
+
+    import paper_2412_14975_gb300 as lib
+    from oracle.recognizer import SerialRecognizer
+    if name == "batch":
+        res, texts = build_batch_workload_host(lib, 64, args.seed)
+        rid = [i % len(res) for i in range(len(texts))]
+    else:
+        res, _, texts, rid = build_served_workload(lib, 32, 128, args.seed)
+    sers = {}
+    order = list(range(len(texts)))
+    for i in range(args.warmup):
+        j = order[i % len(order)]
+        sers.setdefault(rid[j], SerialRecognizer(res[rid[j]])).accepts(texts[j])
+    per_step = 4 << 20
+    svc = []
+    t = time.perf_counter()
+    nbytes = 0
+    pos = 0
+    for _ in range(args.steps):
+        got = 0
+        while got < per_step:
+            j = order[pos % len(order)]
+            pos += 1
+            t1 = time.perf_counter()
+            sers.setdefault(rid[j], SerialRecognizer(res[rid[j]])).accepts(texts[j])
+            svc.append((time.perf_counter() - t1) * 1e3)
+            got += texts[j].size
+        nbytes += got
+    dt = time.perf_counter() - t
+    v = nbytes / dt / 1e9
+    line = {"metric": METRIC, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "impl": "reference",
+            "value": round(v, 6),
+            "config": {"workload": f"{name}: oracle over {per_step} bytes of the workload's texts per step",
+                       "texts_in_sample": len(texts)},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(v, 6), "unit": "GB/s",
+                             "sample": f"{per_step} bytes per step, item by item"},
+            "e2e": {"value": round(v, 6), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if name == "served":
+        # one request at a time: its service time bounds the latency from below (the oracle cannot
+        # keep up with the offered rates, so its queueing latency grows without bound)
+        line["value"] = round(float(np.percentile(svc, 99)), 3)
+        line["unit"] = "ms"
+        line["higher_is_better"] = False
+        line["config"]["note"] = "value = p99 of per-request service time (unloaded); GB/s in cpu_baseline"
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
     name = args.workload
+    if name in ("batch", "served"):
+        run_reference_multi(args, name)
+        return
     re_src = workload_re(name)
     from oracle.recognizer import SerialRecognizer
     ser = SerialRecognizer(re_src)
@@ -185,11 +242,9 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def build_batch_workload(lib, torch, dev, n_texts, seed):
-    """The batched configuration: n_texts texts (lognormal lengths) over 16 REs, resident in one
-    16-byte-aligned device buffer.  Returns (progs, items, total_bytes, device buffer, REs)."""
-    import numpy as np
-
+def select_batch_res(lib, seed):
+    """The batched configuration's 16 REs: the 3 single-text REs and the first 13 random (R)* REs
+    whose RI-DFA has 10..5000 states and at most 256 interface slots."""
     import textgen.batch as tb
     res = tb.standard_res()
     kept = []
@@ -202,7 +257,24 @@ def build_batch_workload(lib, torch, dev, n_texts, seed):
             kept.append((r, body, alpha))
         if len(kept) == 13:
             break
-    res = res + kept
+    return res + kept
+
+
+def build_batch_workload_host(lib, n_texts, seed):
+    """Host side of the batched configuration: (REs, texts); text j uses RE j mod 16."""
+    import textgen.batch as tb
+    res = select_batch_res(lib, seed)
+    texts = [x for _, _, x, _ in tb.batch_texts(res, n_texts, seed + 1)]
+    return [r for r, _, _ in res], texts
+
+
+def build_batch_workload(lib, torch, dev, n_texts, seed):
+    """The batched configuration: n_texts texts (lognormal lengths) over 16 REs, resident in one
+    16-byte-aligned device buffer.  Returns (progs, items, total_bytes, device buffer, REs, texts)."""
+    import numpy as np
+
+    import textgen.batch as tb
+    res = select_batch_res(lib, seed)
     progs = [lib.ridfa_compile(r, build_dfa=False) for r, _, _ in res]
     texts, rid = [], []
     for j, r, x, _ in tb.batch_texts(res, n_texts, seed + 1):
@@ -313,13 +385,143 @@ def run_batch(args, lib, torch, dev, stream, world, rank):
     b.close()
 
 
+def build_served_workload(lib, n_res, n_pool, seed):
+    """The served configuration: n_res resident REs (the 3 single-text REs + random ones) and a pool
+    of host texts (lognormal lengths, median 64 KiB, sigma 1, at most 16 MiB) that requests draw
+    from.  Returns (REs, programs, texts, RE index of each text)."""
+    import numpy as np
+
+    import textgen.batch as tb
+    res = tb.standard_res()
+    for r, body, alpha in tb.random_re_candidates(seed, 2000):
+        if len(res) == n_res:
+            break
+        try:
+            p = lib.ridfa_compile(r, build_dfa=False)
+        except lib.RidfaError:
+            continue
+        if 10 <= p.info["n_states"] <= 5000 and p.info["k"] <= lib.RIDFA_MAX_SLOTS:
+            res.append((r, body, alpha))
+    progs = [lib.ridfa_compile(r, build_dfa=False) for r, _, _ in res]
+    texts, rid = [], []
+    for _, r, x, _ in tb.batch_texts(res, n_pool, seed + 1, median=64 << 10, sigma=1.0):
+        texts.append(np.ascontiguousarray(x[: 16 << 20]))
+        rid.append(r)
+    return [r for r, _, _ in res], progs, texts, rid
+
+
+def run_served(args, lib, torch, dev, rank):
+    """Open-loop Poisson load on the server at each rate: latency = result posted - scheduled
+    arrival (submit lateness + the server's submit-to-result time), so a client that falls behind
+    is charged for it."""
+    import numpy as np
+    t0 = time.perf_counter()
+    res, progs, texts, rid = build_served_workload(lib, 32, args.served_pool, args.seed)
+    gen_s = time.perf_counter() - t0
+    rates = [int(r) for r in args.served_rates.split(",")]
+    rng = np.random.Generator(np.random.PCG64(args.seed + 7))
+    srv = lib.Server(n_streams=3, arena_bytes=4 << 30, max_batch_requests=8192, max_batch_bytes=512 << 20,
+                     chunk_len=args.batch_chunk_len or 8192)
+    slots = [srv.add_program(p) for p in progs]
+    # correctness: served results equal the single-text path on a sample (warms the server too)
+    sample = rng.choice(len(texts), size=min(64, len(texts)), replace=False)
+    want = {}
+    for i in sample:
+        x = texts[i]
+        if x.size == 0:
+            continue
+        d = torch.from_numpy(x).to(dev)
+        want[int(i)] = lib.ridfa_recognize(progs[rid[i]], d, x.size, max(1, min(x.size, 64)))
+    ids = {srv.submit(slots[rid[i]], texts[i]): i for i in want}
+    srv.drain()
+    mism = 0
+    for r_id, st, acc, _ in srv.poll():
+        mism += int(st != 0 or acc != want[ids[r_id]])
+    lens = np.array([x.size for x in texts])
+    results = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for rate in rates:
+            n = max(1, int(rate * args.served_seconds))
+            sched = np.cumsum(rng.exponential(1.0 / rate, size=n))
+            pick = rng.integers(0, len(texts), size=n)
+            late = {}
+            lat = []
+            st0 = srv.stats()
+            nbytes = 0
+            i = 0
+            tstart = time.perf_counter()
+            while i < n or len(lat) < n:
+                now = time.perf_counter() - tstart
+                if i < n and now >= sched[i]:
+                    j = int(pick[i])
+                    r_id = srv.try_submit(slots[rid[j]], texts[j])
+                    if r_id is not None:
+                        late[r_id] = now - sched[i]
+                        nbytes += texts[j].size
+                        i += 1
+                        continue
+                for r_id, st, acc, us in srv.poll(wait_us=0 if i < n else 1000):
+                    lat.append(late.pop(r_id) * 1e3 + us / 1e3)
+            wall = time.perf_counter() - tstart
+            st1 = srv.stats()
+            lat = np.sort(np.array(lat))
+            nb = st1["batches"] - st0["batches"]
+            results.append({"offered_rps": rate, "requests": n, "achieved_rps": round(n / wall, 1),
+                            "GBps": round(nbytes / wall / 1e9, 3),
+                            "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                            "max_ms": round(float(lat[-1]), 3), "batches": nb,
+                            "mean_batch": round(n / max(nb, 1), 1),
+                            "busy_retries": st1["rejected"] - st0["rejected"]})
+    stats = srv.stats()
+    srv.close()
+    # one text per launch on the same request mix: copy, recognise, read the bit, one by one
+    acc1 = torch.zeros(1, dtype=torch.uint8, device=dev)
+    L = args.batch_chunk_len or 8192
+    pin = [torch.from_numpy(texts[j]).pin_memory() for j in range(min(len(texts), 512))]
+    d_buf = torch.empty(max(int(lens.max()), 16), dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    nb1 = 0
+    for j, h in enumerate(pin):
+        n = h.numel()
+        if n == 0:
+            continue
+        d_buf[:n].copy_(h, non_blocking=True)
+        lib.ridfa_recognize(progs[rid[j]], d_buf, n, max(1, min(n, (n + L - 1) // L)))
+        nb1 += n
+    single = {"requests": len(pin), "GBps": round(nb1 / (time.perf_counter() - t0) / 1e9, 3),
+              "rps": round(len(pin) / (time.perf_counter() - t0), 1)}
+    ref = next((r for r in results if r["offered_rps"] == args.served_ref_rate), results[-1])
+    if rank == 0:
+        line = {"metric": METRIC, "value": ref["p99_ms"], "unit": "ms", "n_gpus": 1,
+                "steps": len(rates), "warmup": args.warmup, "ms_per_step": None,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic",
+                "config": {"workload": f"served: Poisson arrivals over {len(res)} resident REs, host texts "
+                                       f"lognormal median 64 KiB sigma 1 (max 16 MiB), {args.served_seconds} s "
+                                       f"per rate; value = p99 at {ref['offered_rps']} req/s",
+                           "pool_texts": len(texts), "pool_mean_bytes": int(lens.mean()),
+                           "generate_s": round(gen_s, 1), "n_streams": 3, "chunk_len": L,
+                           "correctness_sample": len(want), "mismatches": mism},
+                "rates": results, "single_text_per_launch": single,
+                "server_stats": stats, "clocks": clk.summary(),
+                "e2e": {"value": ref["GBps"], "unit": "GB/s", "h2d_bytes_per_step": int(lens.mean()),
+                        "d2h_bytes_per_step": 1},
+                "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["batch", "served"])
+    ap.add_argument("--served-rates", default="2000,5000,10000,20000,50000")
+    ap.add_argument("--served-seconds", type=float, default=5.0)
+    ap.add_argument("--served-ref-rate", type=int, default=10000)
+    ap.add_argument("--served-pool", type=int, default=2048)
     ap.add_argument("--batch-texts", type=int, default=10000)
     ap.add_argument("--batch-chunk-len", type=int, default=0, help="0 = autotune")
     ap.add_argument("--text-bytes", type=int, default=None)
@@ -356,6 +558,11 @@ def main():
     stream = torch.cuda.current_stream()
     if name == "batch":
         run_batch(args, lib, torch, dev, stream, world, rank)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if name == "served":
+        run_served(args, lib, torch, dev, rank)
         if world > 1:
             dist.destroy_process_group()
         return

@@ -254,6 +254,72 @@ int ridfa_recognize_batch(const ridfa_program *const *progs, uint32_t n_progs,
                           const ridfa_batch_item *items, uint32_t n_items, uint8_t *d_accept,
                           void *stream);
 
+/* ---- Served recognition (the paper has no serving layer; each request is recognised exactly
+ * as ridfa_recognize would, reach + join of Sec. 3.2).
+ * A server keeps programs resident and owns one CUDA device: a text arena in device memory with
+ * a pinned host mirror, and n_streams launch slots, each with its own stream, descriptor image
+ * and scratch.  ridfa_server_submit() admits a request (copying a host text into the arena's
+ * mirror) or refuses it with E_BUSY; a scheduler thread forms a batch from every request pending
+ * whenever a launch slot is free (continuous batching: requests that arrive while batches run
+ * join the next one), copies the batch's texts to the device, runs the batched reach and join
+ * on that slot's stream and posts one result per request; ridfa_server_poll() collects them. */
+typedef struct {
+    int32_t device;             /* CUDA device ordinal (-1: the current device) */
+    uint32_t n_streams;         /* launch slots (batches in flight); 0 = 3 */
+    uint64_t arena_bytes;       /* device text arena (and its pinned mirror); 0 = 1 GiB */
+    uint32_t max_requests;      /* requests admitted and not yet polled; 0 = 1 << 20 */
+    uint32_t max_batch_requests;/* requests per batch; 0 = 8192 */
+    uint64_t max_batch_bytes;   /* text bytes per batch; 0 = 512 MiB */
+    uint32_t chunk_len;         /* bytes per chunk; 0 = 8192 */
+    uint32_t reserved;
+} ridfa_server_opts;
+
+typedef struct {
+    uint64_t req_id;
+    int32_t status;             /* RIDFA_OK, or RIDFA_E_STATE / RIDFA_E_CUDA for this request */
+    uint32_t accept;            /* 1 if the text is in L(RE) */
+    double latency_us;          /* submit to result posted, host steady clock */
+} ridfa_result;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, batches, bytes;
+    uint32_t max_batch, n_programs;
+    uint64_t device_bytes;      /* arena + slot scratch */
+} ridfa_server_stats;
+
+typedef struct ridfa_server ridfa_server;
+
+#define RIDFA_SUBMIT_DEVICE_TEXT 1u /* submit flag: `text` is a device pointer, used in place; it
+                                       must stay valid until the request's result is polled */
+
+/* Create a server (opts may be NULL) and start its scheduler thread.
+ * Errors: E_ARG, E_NOMEM, E_CUDA. */
+int ridfa_server_create(const ridfa_server_opts *opts, ridfa_server **out);
+
+/* Make `prog` resident (tables uploaded now) and return its slot for submit().  The program
+ * must outlive the server.  Errors: E_ARG, E_UNSUPPORTED (k > RIDFA_MAX_SLOTS), E_NOMEM, E_CUDA. */
+int ridfa_server_add_program(ridfa_server *srv, const ridfa_program *prog, uint32_t *prog_slot);
+
+/* Submit one request: recognise text[0, len) with program `prog_slot`.  A host text is copied
+ * before the call returns; a device text (RIDFA_SUBMIT_DEVICE_TEXT) is read in place.
+ * Errors: E_ARG, E_BUSY (arena or request budget full: poll, then retry), E_TOO_LARGE (the text
+ * alone exceeds the arena or a batch). */
+int ridfa_server_submit(ridfa_server *srv, uint32_t prog_slot, const uint8_t *text, uint64_t len,
+                        uint32_t flags, uint64_t *req_id);
+
+/* Move up to max finished results to out (*n_out of them), waiting up to wait_us microseconds
+ * for the first one.  Errors: E_ARG. */
+int ridfa_server_poll(ridfa_server *srv, ridfa_result *out, uint32_t max, uint32_t *n_out, uint32_t wait_us);
+
+/* Wait until every submitted request has finished (results may still be unpolled), at most
+ * timeout_ms milliseconds.  Errors: E_ARG, E_TIMEOUT. */
+int ridfa_server_drain(ridfa_server *srv, uint32_t timeout_ms);
+
+int ridfa_server_get_stats(const ridfa_server *srv, ridfa_server_stats *out);
+
+/* Stop the scheduler, wait for work in flight and release everything.  NULL is a no-op. */
+void ridfa_server_destroy(ridfa_server *srv);
+
 /* Roofline microbenchmarks (diagnostics; the paper has no counterpart).  Both allocate a 4-byte
  * sink and synchronise the current device.
  * ridfa_bench_smem_gather: the reach kernel's converged step alone -- per text byte one

@@ -368,3 +368,125 @@ def ridfa_recognize_batch(progs, items, d_accept, stream=None):
     parr, iarr = _batch_arrays(progs, items)
     _check(_lib.ridfa_recognize_batch(parr, len(progs), iarr, len(items), _ptr(d_accept), _stream(stream)),
            "ridfa_recognize_batch")
+
+
+# ---------------------------------------------------------------------------------- serving
+RIDFA_SUBMIT_DEVICE_TEXT = 1
+
+
+class ServerOpts(_c.Structure):
+    _fields_ = [("device", _c.c_int32), ("n_streams", _u32), ("arena_bytes", _c.c_uint64),
+                ("max_requests", _u32), ("max_batch_requests", _u32), ("max_batch_bytes", _c.c_uint64),
+                ("chunk_len", _u32), ("reserved", _u32)]
+
+
+class Result(_c.Structure):
+    _fields_ = [("req_id", _c.c_uint64), ("status", _c.c_int32), ("accept", _u32),
+                ("latency_us", _c.c_double)]
+
+
+class ServerStats(_c.Structure):
+    _fields_ = [("submitted", _c.c_uint64), ("completed", _c.c_uint64), ("rejected", _c.c_uint64),
+                ("batches", _c.c_uint64), ("bytes", _c.c_uint64), ("max_batch", _u32),
+                ("n_programs", _u32), ("device_bytes", _c.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_decl("ridfa_server_create", _c.c_int, [_c.POINTER(ServerOpts), _c.POINTER(_vp)])
+_decl("ridfa_server_add_program", _c.c_int, [_vp, _vp, _c.POINTER(_u32)])
+_decl("ridfa_server_submit", _c.c_int, [_vp, _u32, _vp, _c.c_uint64, _u32, _c.POINTER(_c.c_uint64)])
+_decl("ridfa_server_poll", _c.c_int, [_vp, _c.POINTER(Result), _u32, _c.POINTER(_u32), _u32])
+_decl("ridfa_server_drain", _c.c_int, [_vp, _u32])
+_decl("ridfa_server_get_stats", _c.c_int, [_vp, _c.POINTER(ServerStats)])
+_decl("ridfa_server_destroy", None, [_vp])
+
+
+class Server:
+    """Owns one ridfa_server*; keeps its programs alive.
+
+    submit() takes a host text (bytes, bytearray or a contiguous uint8 numpy array), copied into
+    the server's arena before it returns, or a CUDA uint8 tensor / device address with
+    device=True (read in place: keep it alive until its result is polled)."""
+
+    def __init__(self, device=-1, n_streams=0, arena_bytes=0, max_requests=0, max_batch_requests=0,
+                 max_batch_bytes=0, chunk_len=0):
+        opts = ServerOpts(int(device), int(n_streams), int(arena_bytes), int(max_requests),
+                          int(max_batch_requests), int(max_batch_bytes), int(chunk_len), 0)
+        h = _vp()
+        _check(_lib.ridfa_server_create(_c.byref(opts), _c.byref(h)), "ridfa_server_create")
+        self.handle = h.value
+        self.progs = []
+        self._res = (Result * 4096)()
+
+    def add_program(self, prog):
+        slot = _u32()
+        _check(_lib.ridfa_server_add_program(self, prog, _c.byref(slot)), "ridfa_server_add_program")
+        self.progs.append(prog)
+        return slot.value
+
+    def submit(self, prog_slot, text, length=None, device=False):
+        """Returns the request id; raises RidfaError (code -8, E_BUSY) when admission is refused."""
+        if device:
+            ptr = _ptr(text)
+            n = int(length if length is not None else text.numel())
+            flags = RIDFA_SUBMIT_DEVICE_TEXT
+        else:
+            if isinstance(text, (bytes, bytearray)):
+                buf = np.frombuffer(text, dtype=np.uint8)
+            else:
+                buf = np.ascontiguousarray(text, dtype=np.uint8)
+            n = int(length if length is not None else buf.size)
+            ptr = buf.ctypes.data if n else None
+            flags = 0
+        rid = _c.c_uint64()
+        _check(_lib.ridfa_server_submit(self, int(prog_slot), ptr, n, flags, _c.byref(rid)), "ridfa_server_submit")
+        return rid.value
+
+    def try_submit(self, prog_slot, text, length=None, device=False):
+        """As submit(), but returns None instead of raising when the server is busy."""
+        try:
+            return self.submit(prog_slot, text, length, device)
+        except RidfaError as e:
+            if e.code == -8:
+                return None
+            raise
+
+    def poll(self, max_results=4096, wait_us=0):
+        """List of (req_id, status, accept, latency_us)."""
+        n = _u32()
+        m = min(int(max_results), len(self._res))
+        _check(_lib.ridfa_server_poll(self, self._res, m, _c.byref(n), int(wait_us)), "ridfa_server_poll")
+        return [(r.req_id, r.status, bool(r.accept), r.latency_us) for r in self._res[:n.value]]
+
+    def drain(self, timeout_ms=60_000):
+        _check(_lib.ridfa_server_drain(self, int(timeout_ms)), "ridfa_server_drain")
+
+    def stats(self):
+        st = ServerStats()
+        _check(_lib.ridfa_server_get_stats(self, _c.byref(st)), "ridfa_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self.handle:
+            _lib.ridfa_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        if not self.handle:
+            raise ValueError("server is closed")
+        return self.handle

@@ -25,6 +25,7 @@
 #include <tuple>
 #include <vector>
 
+#include "ridfa_batch_plan.h"
 #include "ridfa_internal.h"
 #include "ridfa_kernels.cuh"
 
@@ -440,13 +441,16 @@ struct LaunchGroup {          // one persistent reach launch
     std::vector<uint32_t> progs;   // batch program indices in this launch
     uint32_t task0 = 0, n_tasks = 0;
     size_t table_smem = 0;
+    int block = 0, grid = 0;
+    uint32_t stg = 0;              // staging offset in dynamic shared memory
+    size_t smem = 0;               // dynamic shared memory
 };
 
 template <int R, class LUT, bool COOP>
 cudaError_t batch_reach_one(const BatchReachArgs &a, int grid, int block, size_t smem, uint32_t stg,
                             cudaStream_t st, int *per_sm) {
     auto kern = rid_reach_batch_kernel<R, LUT, (R <= 4 ? 1024 : 512), COOP>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = ensure_smem_cap(reinterpret_cast<const void *>(kern), smem);
     if (e != cudaSuccess) return e;
     if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, block, smem);
     kern<<<grid, block, smem, st>>>(a, stg);
@@ -464,20 +468,38 @@ cudaError_t batch_reach_r(int R, const BatchReachArgs &a, int grid, int block, s
     }
 }
 
-cudaError_t batch_reach(const LaunchGroup &g, const BatchReachArgs &a, int grid, int block, size_t smem,
-                        uint32_t stg, cudaStream_t st, int *per_sm) {
+cudaError_t batch_reach(const LaunchGroup &g, const BatchReachArgs &a, cudaStream_t st, int *per_sm) {
     if (g.coop) {
         switch (g.mode) {
-            case kBRep16: return batch_reach_r<LutRep<true>, true>(g.R, a, grid, block, smem, stg, st, per_sm);
-            case kBRep32: return batch_reach_r<LutRep<false>, true>(g.R, a, grid, block, smem, stg, st, per_sm);
-            default: return batch_reach_r<LutPlain, true>(g.R, a, grid, block, smem, stg, st, per_sm);
+            case kBRep16: return batch_reach_r<LutRep<true>, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+            case kBRep32: return batch_reach_r<LutRep<false>, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+            default: return batch_reach_r<LutPlain, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
         }
     }
     switch (g.mode) {
-        case kBRep16: return batch_reach_r<LutRep<true>, false>(g.R, a, grid, block, smem, stg, st, per_sm);
-        case kBRep32: return batch_reach_r<LutRep<false>, false>(g.R, a, grid, block, smem, stg, st, per_sm);
-        default: return batch_reach_r<LutPlain, false>(g.R, a, grid, block, smem, stg, st, per_sm);
+        case kBRep16: return batch_reach_r<LutRep<true>, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+        case kBRep32: return batch_reach_r<LutRep<false>, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+        default: return batch_reach_r<LutPlain, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
     }
+}
+
+// Resident blocks per SM of a launch group's kernel, cached: setting the shared-memory attribute
+// and querying occupancy once per (device, layout, R, path, block, shared memory).
+int blocks_per_sm(int device, const LaunchGroup &g, int *per_sm) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, uint32_t, int, bool, int, size_t>, int> cache;
+    const auto key = std::make_tuple(device, g.mode, g.R, g.coop, g.block, g.smem);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *per_sm = it->second;
+        return RIDFA_OK;
+    }
+    BatchReachArgs a{};
+    cudaError_t e = batch_reach(g, a, nullptr, per_sm);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cache[key] = *per_sm;
+    return RIDFA_OK;
 }
 
 inline size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -492,6 +514,233 @@ int log2i(uint32_t v) {
 }
 
 }  // namespace
+
+struct BatchPlan {
+    std::vector<const ridfa_program *> progs;
+    std::vector<const DeviceAutomaton *> dev;
+    std::vector<uint32_t> tis, n_texts_of, text0;
+    std::vector<uint64_t> maps_off, dinfo_off;   // within the maps / summaries regions
+    std::vector<TextDesc> texts;                 // grouped by program
+    std::vector<TaskDesc> tasks;
+    std::vector<SegDesc> segs;
+    std::vector<LaunchGroup> groups;
+    uint32_t n_items = 0;
+    uint64_t total_bytes = 0, total_chunks = 0;
+    // block layout; everything before o_part is the host image
+    size_t o_counters = 0, o_progs = 0, o_texts = 0, o_tasks = 0, o_segs = 0, o_tick = 0, o_flags = 0;
+    size_t o_part = 0, o_runs = 0, o_finals = 0, o_maps = 0, o_dinfo = 0, total = 0;
+};
+
+BatchPlan *plan_new() { return new (std::nothrow) BatchPlan(); }
+void plan_delete(BatchPlan *pl) { delete pl; }
+size_t plan_device_bytes(const BatchPlan *pl) { return pl->total; }
+size_t plan_image_bytes(const BatchPlan *pl) { return pl->o_part; }
+size_t plan_status_offset(const BatchPlan *pl) { return pl->o_counters + 32 * 4; }
+
+PlanStats plan_stats(const BatchPlan *pl) {
+    PlanStats s{};
+    s.total_bytes = pl->total_bytes;
+    s.total_chunks = pl->total_chunks;
+    s.n_programs = static_cast<uint32_t>(pl->progs.size());
+    s.n_launches = static_cast<uint32_t>(pl->groups.size()) + (pl->segs.empty() ? 0 : 1);
+    s.n_tasks = static_cast<uint32_t>(pl->tasks.size());
+    s.n_segments = static_cast<uint32_t>(pl->segs.size());
+    return s;
+}
+
+int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, const ridfa_batch_item *items,
+               uint32_t ni, uint32_t L, int device) {
+    if (!pl || !progs || !np || (ni && !items) || L == 0) return RIDFA_E_ARG;
+    for (uint32_t p = 0; p < np; ++p)
+        if (!progs[p] || progs[p]->rid.k > RIDFA_MAX_SLOTS) return progs[p] ? RIDFA_E_UNSUPPORTED : RIDFA_E_ARG;
+    for (uint32_t i = 0; i < ni; ++i) {
+        const ridfa_batch_item &it = items[i];
+        if (it.prog >= np || (it.len && !it.d_text)) return RIDFA_E_ARG;
+        if (it.n_chunks > it.len || (it.len == 0 && it.n_chunks)) return RIDFA_E_CHUNKS;
+    }
+    BatchPlan &P = *pl;
+    P.progs.assign(progs, progs + np);
+    P.n_items = ni;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024 - 64;
+    // per-program device tables and layout
+    P.dev.assign(np, nullptr);
+    std::vector<uint32_t> mode(np, kBPlain);
+    P.tis.assign(np, 0);
+    std::vector<size_t> tbytes(np, 0);
+    for (uint32_t p = 0; p < np; ++p) {
+        const ridfa_program *R = progs[p];
+        std::lock_guard<std::mutex> lock(R->mu);
+        int err = RIDFA_OK;
+        P.dev[p] = device_copy(R, false, device, &err);
+        if (!P.dev[p]) return err;
+        const HostAutomaton &H = R->rid;
+        Automaton A{nullptr, nullptr, nullptr, nullptr, nullptr, H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+        const size_t r16 = LutRep<true>::smem_bytes(A), r32 = LutRep<false>::smem_bytes(A), pln = LutPlain::smem_bytes(A);
+        if (LutRep<true>::fits16(A) && r16 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep16; tbytes[p] = r16; }
+        else if (r32 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep32; tbytes[p] = r32; }
+        else if (pln + 8 * kWarpCoopBytes <= limit) { mode[p] = kBPlain; P.tis[p] = 1; tbytes[p] = pln; }
+        else { mode[p] = kBPlain; P.tis[p] = 0; tbytes[p] = 256; }
+    }
+    // texts grouped by program; chunk counts
+    std::vector<std::vector<uint32_t>> by_prog(np);
+    for (uint32_t i = 0; i < ni; ++i) by_prog[items[i].prog].push_back(i);
+    P.texts.clear();
+    std::vector<uint64_t> prog_chunks(np, 0);
+    P.text0.assign(np, 0);
+    P.n_texts_of.assign(np, 0);
+    bool aligned_all = true;
+    P.total_bytes = 0;
+    for (uint32_t p = 0; p < np; ++p) {
+        P.text0[p] = static_cast<uint32_t>(P.texts.size());
+        P.n_texts_of[p] = static_cast<uint32_t>(by_prog[p].size());
+        for (uint32_t i : by_prog[p]) {
+            const ridfa_batch_item &it = items[i];
+            TextDesc td{it.d_text, it.len, prog_chunks[p], 0, i};
+            if (it.len == 0) td.c = 0;
+            else if (it.n_chunks) td.c = it.n_chunks;
+            else td.c = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(it.len, (it.len + L - 1) / L)));
+            if (it.len && (reinterpret_cast<uintptr_t>(it.d_text) & 15)) aligned_all = false;
+            prog_chunks[p] += td.c;
+            P.total_bytes += it.len;
+            P.texts.push_back(td);
+        }
+    }
+    P.total_chunks = 0;
+    for (uint32_t p = 0; p < np; ++p) P.total_chunks += prog_chunks[p];
+    // launch groups by layout; tasks ordered by group then program
+    P.groups.clear();
+    P.tasks.clear();
+    uint64_t run_warps = 0;
+    for (uint32_t m = kBPlain; m <= kBRep32; ++m) {
+        LaunchGroup g;
+        g.mode = m;
+        g.coop = aligned_all;
+        for (uint32_t p = 0; p < np; ++p)
+            if (mode[p] == m && prog_chunks[p]) {
+                g.progs.push_back(p);
+                const uint32_t k = progs[p]->rid.k;
+                g.R = std::max(g.R, k <= 32 ? 1 : k <= 64 ? 2 : k <= 128 ? 4 : 8);
+                g.table_smem = std::max(g.table_smem, tbytes[p]);
+            }
+        if (g.progs.empty()) continue;
+        g.task0 = static_cast<uint32_t>(P.tasks.size());
+        const int cap = g.R <= 4 ? 1024 : 512;
+        g.stg = static_cast<uint32_t>((g.table_smem + 127) & ~static_cast<size_t>(127));
+        int warps = g.coop ? static_cast<int>(std::min<size_t>(cap / 32, (limit - g.stg) / kWarpCoopBytes)) : cap / 32;
+        warps = std::max(warps, 1);
+        g.block = warps * 32;
+        g.smem = g.coop ? g.stg + static_cast<size_t>(warps) * kWarpCoopBytes : g.table_smem;
+        const uint64_t per_task = 32ull * warps;
+        for (uint32_t p : g.progs)
+            for (uint64_t c0 = 0; c0 < prog_chunks[p]; c0 += per_task)
+                P.tasks.push_back(TaskDesc{c0, p, static_cast<uint32_t>(std::min<uint64_t>(per_task, prog_chunks[p] - c0))});
+        g.n_tasks = static_cast<uint32_t>(P.tasks.size()) - g.task0;
+        // persistent: as many blocks as fit on every SM, no more than there are tasks
+        int per_sm = 0;
+        const int err = blocks_per_sm(device, g, &per_sm);
+        if (err != RIDFA_OK) return err;
+        if (per_sm < 1) return RIDFA_E_UNSUPPORTED;
+        g.grid = static_cast<int>(std::min<uint64_t>(g.n_tasks, static_cast<uint64_t>(sms) * per_sm));
+        run_warps = std::max<uint64_t>(run_warps, static_cast<uint64_t>(g.grid) * warps);
+        P.groups.push_back(g);
+    }
+    // join segments
+    P.segs.clear();
+    for (uint32_t p = 0; p < np; ++p)
+        for (uint32_t t = P.text0[p]; t < P.text0[p] + P.n_texts_of[p]; ++t) {
+            const TextDesc &td = P.texts[t];
+            const uint64_t nb = td.c > 1 ? td.c - 1 : 0;
+            const uint32_t nseg = nb ? static_cast<uint32_t>((nb + kBatchJoinThreads - 1) / kBatchJoinThreads) : 1;
+            const uint32_t part0 = static_cast<uint32_t>(P.segs.size());
+            for (uint32_t sgi = 0; sgi < nseg; ++sgi) {
+                const uint64_t b0 = 1 + static_cast<uint64_t>(sgi) * kBatchJoinThreads;
+                const uint32_t cnt = nb ? static_cast<uint32_t>(std::min<uint64_t>(kBatchJoinThreads, nb + 1 - b0)) : 0;
+                P.segs.push_back(SegDesc{b0, p, t, cnt, sgi, nseg, part0});
+            }
+        }
+    // block layout: the host image first, then device-only scratch
+    uint64_t maps_bytes = 0, dinfo_bytes = 0;
+    P.maps_off.assign(np, 0);
+    P.dinfo_off.assign(np, 0);
+    for (uint32_t p = 0; p < np; ++p) {
+        P.maps_off[p] = maps_bytes;
+        P.dinfo_off[p] = dinfo_bytes;
+        maps_bytes += al256(prog_chunks[p] * progs[p]->rid.k * 2);
+        dinfo_bytes += al256(prog_chunks[p] * 4);
+    }
+    size_t off = 0;
+    P.o_counters = off; off += 256;
+    P.o_progs = off;    off += al256(np * sizeof(ProgDesc));
+    P.o_texts = off;    off += al256(P.texts.size() * sizeof(TextDesc));
+    P.o_tasks = off;    off += al256(P.tasks.size() * sizeof(TaskDesc));
+    P.o_segs = off;     off += al256(P.segs.size() * sizeof(SegDesc));
+    P.o_tick = off;     off += al256(P.texts.size() * 4);
+    P.o_flags = off;    off += al256(P.texts.size() * 4);
+    P.o_part = off;     off += al256(P.segs.size() * kPartialWords * 4);
+    P.o_runs = off;     off += al256(run_warps * kRunsPerWarp * sizeof(RunEntry));
+    P.o_finals = off;   off += al256(run_warps * kFinalsPerWarp * 4);
+    P.o_maps = off;     off += maps_bytes;
+    P.o_dinfo = off;    off += dinfo_bytes;
+    P.total = off;
+    return RIDFA_OK;
+}
+
+void plan_image(const BatchPlan *pl, uint8_t *base, uint8_t *img) {
+    const BatchPlan &P = *pl;
+    std::memset(img, 0, P.o_part);
+    const uint32_t np = static_cast<uint32_t>(P.progs.size());
+    ProgDesc *pd = reinterpret_cast<ProgDesc *>(img + P.o_progs);
+    for (uint32_t p = 0; p < np; ++p) {
+        const HostAutomaton &H = P.progs[p]->rid;
+        const DeviceAutomaton *D = P.dev[p];
+        pd[p].A = Automaton{D->trans, D->classmap, D->final_bits, D->ifmask, D->slot_state,
+                            H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+        pd[p].texts = reinterpret_cast<const TextDesc *>(base + P.o_texts) + P.text0[p];
+        pd[p].maps = reinterpret_cast<uint16_t *>(base + P.o_maps + P.maps_off[p]);
+        pd[p].dinfo = reinterpret_cast<uint32_t *>(base + P.o_dinfo + P.dinfo_off[p]);
+        pd[p].n_texts = P.n_texts_of[p];
+        pd[p].tis = P.tis[p];
+        pd[p].text0 = P.text0[p];
+        pd[p].pad = 0;
+    }
+    if (!P.texts.empty()) std::memcpy(img + P.o_texts, P.texts.data(), P.texts.size() * sizeof(TextDesc));
+    if (!P.tasks.empty()) std::memcpy(img + P.o_tasks, P.tasks.data(), P.tasks.size() * sizeof(TaskDesc));
+    if (!P.segs.empty()) std::memcpy(img + P.o_segs, P.segs.data(), P.segs.size() * sizeof(SegDesc));
+}
+
+int plan_enqueue(const BatchPlan *pl, uint8_t *base, uint8_t *d_accept, cudaStream_t st, bool zero_counters) {
+    const BatchPlan &P = *pl;
+    uint32_t *counters = reinterpret_cast<uint32_t *>(base + P.o_counters);
+    uint32_t *status = counters + 32;
+    if (zero_counters) {
+        cudaError_t e = cudaMemsetAsync(counters, 0, 256, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    const ProgDesc *progs = reinterpret_cast<const ProgDesc *>(base + P.o_progs);
+    const TaskDesc *tasks = reinterpret_cast<const TaskDesc *>(base + P.o_tasks);
+    RunEntry *runs = reinterpret_cast<RunEntry *>(base + P.o_runs);
+    uint32_t *finals = reinterpret_cast<uint32_t *>(base + P.o_finals);
+    for (size_t gi = 0; gi < P.groups.size(); ++gi) {
+        const LaunchGroup &g = P.groups[gi];
+        if (g.n_tasks == 0) continue;
+        BatchReachArgs a{progs, tasks + g.task0, g.n_tasks, 8, counters + gi, status, runs, finals};
+        cudaError_t e = batch_reach(g, a, st, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (!P.segs.empty()) {
+        BatchJoinArgs J{progs, reinterpret_cast<const TextDesc *>(base + P.o_texts),
+                        reinterpret_cast<const SegDesc *>(base + P.o_segs),
+                        reinterpret_cast<uint32_t *>(base + P.o_part), reinterpret_cast<uint32_t *>(base + P.o_tick),
+                        reinterpret_cast<uint32_t *>(base + P.o_flags), d_accept, status};
+        rid_join_batch_kernel<<<static_cast<unsigned>(P.segs.size()), kBatchJoinThreads, 0, st>>>(J);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return RIDFA_OK;
+}
+
 }  // namespace ridfa
 
 struct ridfa_batch {
@@ -501,26 +750,11 @@ struct ridfa_batch {
     uint8_t *d_accept = nullptr;
     uint32_t chunk_len = 0;
     bool use_graph = true;
-    // device state
+    ridfa::BatchPlan *plan = nullptr;
     void *dmem = nullptr;
     size_t dbytes = 0;
-    std::vector<ridfa::LaunchGroup> groups;
-    ridfa::ProgDesc *d_progs = nullptr;
-    ridfa::TextDesc *d_texts = nullptr;
-    ridfa::TaskDesc *d_tasks = nullptr;
-    ridfa::SegDesc *d_segs = nullptr;
-    uint32_t *d_partials = nullptr, *d_tickets = nullptr, *d_flags = nullptr, *d_counters = nullptr,
-             *d_status = nullptr, *d_finals = nullptr;
-    ridfa::RunEntry *d_runs = nullptr;
-    uint32_t n_segs = 0, n_texts = 0, n_tasks = 0;
-    uint64_t total_bytes = 0, total_chunks = 0;
-    int grid = 0, block = 0;
-    std::vector<size_t> smem;
-    std::vector<uint32_t> stg;
-    std::vector<int> grids, blocks;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    uint32_t *h_status = nullptr;
 };
 
 namespace ridfa {
@@ -533,209 +767,35 @@ void batch_release(ridfa_batch *B) {
     B->graph = nullptr;
     if (B->dmem) cudaFree(B->dmem);
     B->dmem = nullptr;
+    B->dbytes = 0;
 }
 
-// Enqueue the whole batch (memsets, reach launches, join launch) on `st`.
-int batch_enqueue(ridfa_batch *B, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(B->d_counters, 0, 256, st);   // task tickets and status
-    if (e != cudaSuccess) return cuda_fail(e);
-    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
-        const LaunchGroup &g = B->groups[gi];
-        if (g.n_tasks == 0) continue;
-        BatchReachArgs a{B->d_progs, B->d_tasks + g.task0, g.n_tasks, 8, B->d_counters + gi, B->d_status,
-                         B->d_runs, B->d_finals};
-        e = batch_reach(g, a, B->grids[gi], B->blocks[gi], B->smem[gi], B->stg[gi], st, nullptr);
-        if (e != cudaSuccess) return cuda_fail(e);
-    }
-    if (B->n_segs) {
-        BatchJoinArgs J{B->d_progs, B->d_texts, B->d_segs, B->d_partials, B->d_tickets, B->d_flags,
-                        B->d_accept, B->d_status};
-        rid_join_batch_kernel<<<B->n_segs, kBatchJoinThreads, 0, st>>>(J);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e);
-    }
-    return RIDFA_OK;
-}
-
-// Plan and allocate the batch for chunk length L (items with n_chunks == 0 use ceil(len / L)).
+// Plan and allocate the batch for chunk length L, write its image and capture the graph.
 int batch_build(ridfa_batch *B, uint32_t L) {
     batch_release(B);
-    B->blocks.clear();
-    B->stg.clear();
-    B->smem.clear();
-    B->grids.clear();
-    const uint32_t np = static_cast<uint32_t>(B->progs.size());
-    const uint32_t ni = static_cast<uint32_t>(B->items.size());
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device);
-    const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024 - 64;
-    // per-program device tables and layout
-    std::vector<const DeviceAutomaton *> dev(np, nullptr);
-    std::vector<uint32_t> mode(np, kBPlain), tis(np, 0);
-    std::vector<size_t> tbytes(np, 0);
-    for (uint32_t p = 0; p < np; ++p) {
-        const ridfa_program *P = B->progs[p];
-        std::lock_guard<std::mutex> lock(P->mu);
-        int err = RIDFA_OK;
-        dev[p] = device_copy(P, false, B->device, &err);
-        if (!dev[p]) return err;
-        const HostAutomaton &H = P->rid;
-        Automaton A{nullptr, nullptr, nullptr, nullptr, nullptr, H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
-        const size_t r16 = LutRep<true>::smem_bytes(A), r32 = LutRep<false>::smem_bytes(A), pl = LutPlain::smem_bytes(A);
-        if (LutRep<true>::fits16(A) && r16 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep16; tbytes[p] = r16; }
-        else if (r32 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep32; tbytes[p] = r32; }
-        else if (pl + 8 * kWarpCoopBytes <= limit) { mode[p] = kBPlain; tis[p] = 1; tbytes[p] = pl; }
-        else { mode[p] = kBPlain; tis[p] = 0; tbytes[p] = 256; }
+    if (!B->plan) B->plan = plan_new();
+    if (!B->plan) return RIDFA_E_NOMEM;
+    int err = plan_build(B->plan, B->progs.data(), static_cast<uint32_t>(B->progs.size()), B->items.data(),
+                         static_cast<uint32_t>(B->items.size()), L, B->device);
+    if (err != RIDFA_OK) return err;
+    const size_t total = plan_device_bytes(B->plan);
+    cudaError_t e = cudaMalloc(&B->dmem, total);
+    if (e != cudaSuccess) {
+        B->dmem = nullptr;
+        return cuda_fail(e);
     }
-    // texts grouped by program; chunk counts
-    std::vector<std::vector<uint32_t>> by_prog(np);
-    for (uint32_t i = 0; i < ni; ++i) by_prog[B->items[i].prog].push_back(i);
-    std::vector<TextDesc> texts;
-    std::vector<uint64_t> prog_chunks(np, 0);
-    std::vector<uint32_t> text0(np, 0);
-    bool aligned_all = true;
-    B->total_bytes = 0;
-    for (uint32_t p = 0; p < np; ++p) {
-        text0[p] = static_cast<uint32_t>(texts.size());
-        for (uint32_t i : by_prog[p]) {
-            const ridfa_batch_item &it = B->items[i];
-            TextDesc td{it.d_text, it.len, prog_chunks[p], 0, i};
-            if (it.len == 0) td.c = 0;
-            else if (it.n_chunks) td.c = it.n_chunks;
-            else td.c = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(it.len, (it.len + L - 1) / L)));
-            if (it.len && (reinterpret_cast<uintptr_t>(it.d_text) & 15)) aligned_all = false;
-            prog_chunks[p] += td.c;
-            B->total_bytes += it.len;
-            texts.push_back(td);
-        }
-    }
-    B->n_texts = static_cast<uint32_t>(texts.size());
-    B->total_chunks = 0;
-    for (uint32_t p = 0; p < np; ++p) B->total_chunks += prog_chunks[p];
-    // launch groups by layout; tasks ordered by group then program
-    B->groups.clear();
-    std::vector<TaskDesc> tasks;
-    for (uint32_t m = kBPlain; m <= kBRep32; ++m) {
-        LaunchGroup g;
-        g.mode = m;
-        g.coop = aligned_all;
-        for (uint32_t p = 0; p < np; ++p)
-            if (mode[p] == m && prog_chunks[p]) {
-                g.progs.push_back(p);
-                const uint32_t k = B->progs[p]->rid.k;
-                g.R = std::max(g.R, k <= 32 ? 1 : k <= 64 ? 2 : k <= 128 ? 4 : 8);
-                g.table_smem = std::max(g.table_smem, tbytes[p]);
-            }
-        if (g.progs.empty()) continue;
-        g.task0 = static_cast<uint32_t>(tasks.size());
-        const int cap = g.R <= 4 ? 1024 : 512;
-        const uint32_t stg = static_cast<uint32_t>((g.table_smem + 127) & ~static_cast<size_t>(127));
-        int warps = g.coop ? static_cast<int>(std::min<size_t>(cap / 32, (limit - stg) / kWarpCoopBytes)) : cap / 32;
-        warps = std::max(warps, 1);
-        const uint64_t per_task = 32ull * warps;
-        for (uint32_t p : g.progs)
-            for (uint64_t c0 = 0; c0 < prog_chunks[p]; c0 += per_task)
-                tasks.push_back(TaskDesc{c0, p, static_cast<uint32_t>(std::min<uint64_t>(per_task, prog_chunks[p] - c0))});
-        g.n_tasks = static_cast<uint32_t>(tasks.size()) - g.task0;
-        B->groups.push_back(g);
-        B->blocks.push_back(warps * 32);
-        B->stg.push_back(stg);
-        B->smem.push_back(g.coop ? stg + static_cast<size_t>(warps) * kWarpCoopBytes : g.table_smem);
-    }
-    B->n_tasks = static_cast<uint32_t>(tasks.size());
-    // join segments
-    std::vector<SegDesc> segs;
-    for (uint32_t t = 0; t < B->n_texts; ++t) {
-        const TextDesc &td = texts[t];
-        uint32_t prog = 0;
-        for (uint32_t p = 0; p < np; ++p)
-            if (t >= text0[p] && t < text0[p] + by_prog[p].size()) prog = p;
-        const uint64_t nb = td.c > 1 ? td.c - 1 : 0;
-        const uint32_t nseg = nb ? static_cast<uint32_t>((nb + kBatchJoinThreads - 1) / kBatchJoinThreads) : 1;
-        const uint32_t part0 = static_cast<uint32_t>(segs.size());
-        for (uint32_t sgi = 0; sgi < nseg; ++sgi) {
-            const uint64_t b0 = 1 + static_cast<uint64_t>(sgi) * kBatchJoinThreads;
-            const uint32_t cnt = nb ? static_cast<uint32_t>(std::min<uint64_t>(kBatchJoinThreads, nb + 1 - b0)) : 0;
-            segs.push_back(SegDesc{b0, prog, t, cnt, sgi, nseg, part0});
-        }
-    }
-    B->n_segs = static_cast<uint32_t>(segs.size());
-    // launch shapes: one block per SM (as many as fit), persistent; the groups run one after
-    // another, so they share one run list sized for the largest
-    B->grids.assign(B->groups.size(), 0);
-    uint64_t run_warps = 0;
-    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
-        int per_sm = 0;
-        BatchReachArgs a{};
-        cudaError_t eo = batch_reach(B->groups[gi], a, 0, B->blocks[gi], B->smem[gi], B->stg[gi], nullptr, &per_sm);
-        if (eo != cudaSuccess) return cuda_fail(eo);
-        if (per_sm < 1) return RIDFA_E_UNSUPPORTED;
-        B->grids[gi] = static_cast<int>(std::min<uint64_t>(B->groups[gi].n_tasks, static_cast<uint64_t>(sms) * per_sm));
-        run_warps = std::max<uint64_t>(run_warps, static_cast<uint64_t>(B->grids[gi]) * (B->blocks[gi] / 32));
-    }
-    // one device allocation
-    uint64_t maps_bytes = 0, dinfo_bytes = 0;
-    std::vector<uint64_t> maps_off(np), dinfo_off(np);
-    for (uint32_t p = 0; p < np; ++p) {
-        maps_off[p] = maps_bytes;
-        dinfo_off[p] = dinfo_bytes;
-        maps_bytes += al256(prog_chunks[p] * B->progs[p]->rid.k * 2);
-        dinfo_bytes += al256(prog_chunks[p] * 4);
-    }
-    size_t off = 0;
-    const size_t o_counters = off; off += 256;
-    const size_t o_progs = off;    off += al256(np * sizeof(ProgDesc));
-    const size_t o_texts = off;    off += al256(texts.size() * sizeof(TextDesc));
-    const size_t o_tasks = off;    off += al256(tasks.size() * sizeof(TaskDesc));
-    const size_t o_segs = off;     off += al256(segs.size() * sizeof(SegDesc));
-    const size_t o_part = off;     off += al256(segs.size() * kPartialWords * 4);
-    const size_t o_tick = off;     off += al256(texts.size() * 4);
-    const size_t o_flags = off;    off += al256(texts.size() * 4);
-    const size_t o_runs = off;     off += al256(run_warps * kRunsPerWarp * sizeof(RunEntry));
-    const size_t o_finals = off;   off += al256(run_warps * kFinalsPerWarp * 4);
-    const size_t o_maps = off;     off += maps_bytes;
-    const size_t o_dinfo = off;    off += dinfo_bytes;
-    cudaError_t e = cudaMalloc(&B->dmem, off);
-    if (e != cudaSuccess) return cuda_fail(e);
-    B->dbytes = off;
+    B->dbytes = total;
     uint8_t *base = static_cast<uint8_t *>(B->dmem);
-    B->d_counters = reinterpret_cast<uint32_t *>(base + o_counters);
-    B->d_status = B->d_counters + 32;
-    B->d_progs = reinterpret_cast<ProgDesc *>(base + o_progs);
-    B->d_texts = reinterpret_cast<TextDesc *>(base + o_texts);
-    B->d_tasks = reinterpret_cast<TaskDesc *>(base + o_tasks);
-    B->d_segs = reinterpret_cast<SegDesc *>(base + o_segs);
-    B->d_partials = reinterpret_cast<uint32_t *>(base + o_part);
-    B->d_tickets = reinterpret_cast<uint32_t *>(base + o_tick);
-    B->d_flags = reinterpret_cast<uint32_t *>(base + o_flags);
-    B->d_runs = reinterpret_cast<RunEntry *>(base + o_runs);
-    B->d_finals = reinterpret_cast<uint32_t *>(base + o_finals);
-    std::vector<ProgDesc> pd(np);
-    for (uint32_t p = 0; p < np; ++p) {
-        const HostAutomaton &H = B->progs[p]->rid;
-        const DeviceAutomaton *D = dev[p];
-        pd[p].A = Automaton{D->trans, D->classmap, D->final_bits, D->ifmask, D->slot_state,
-                            H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
-        pd[p].texts = B->d_texts + text0[p];
-        pd[p].maps = reinterpret_cast<uint16_t *>(base + o_maps + maps_off[p]);
-        pd[p].dinfo = reinterpret_cast<uint32_t *>(base + o_dinfo + dinfo_off[p]);
-        pd[p].n_texts = static_cast<uint32_t>(by_prog[p].size());
-        pd[p].tis = tis[p];
-        pd[p].text0 = text0[p];
-    }
-    e = cudaMemset(base, 0, o_maps);
-    if (e == cudaSuccess) e = cudaMemcpy(B->d_progs, pd.data(), np * sizeof(ProgDesc), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !texts.empty()) e = cudaMemcpy(B->d_texts, texts.data(), texts.size() * sizeof(TextDesc), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !tasks.empty()) e = cudaMemcpy(B->d_tasks, tasks.data(), tasks.size() * sizeof(TaskDesc), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !segs.empty()) e = cudaMemcpy(B->d_segs, segs.data(), segs.size() * sizeof(SegDesc), cudaMemcpyHostToDevice);
+    std::vector<uint8_t> img(plan_image_bytes(B->plan));
+    plan_image(B->plan, base, img.data());
+    e = cudaMemcpy(base, img.data(), img.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e);
-    // capture into a graph
     if (B->use_graph) {
         cudaStream_t cs;
         e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e);
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        int err = e == cudaSuccess ? batch_enqueue(B, cs) : cuda_fail(e);
+        err = e == cudaSuccess ? plan_enqueue(B->plan, base, B->d_accept, cs, true) : cuda_fail(e);
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
@@ -756,7 +816,7 @@ int batch_run(ridfa_batch *B, cudaStream_t st) {
         cudaError_t e = cudaGraphLaunch(B->exec, st);
         return e == cudaSuccess ? RIDFA_OK : cuda_fail(e);
     }
-    return batch_enqueue(B, st);
+    return plan_enqueue(B->plan, static_cast<uint8_t *>(B->dmem), B->d_accept, st, true);
 }
 
 // Chunk length for the batch.  Every program is keyed by (log2 |P|, log2 k, log2 C); when all
@@ -856,6 +916,7 @@ extern "C" int ridfa_batch_create(const ridfa_program *const *progs, uint32_t n_
     if (err == RIDFA_OK) err = ridfa::batch_build(B, L);
     if (err != RIDFA_OK) {
         ridfa::batch_release(B);
+        ridfa::plan_delete(B->plan);
         delete B;
         return err;
     }
@@ -872,12 +933,13 @@ extern "C" int ridfa_batch_run(ridfa_batch *b, void *stream) {
 extern "C" int ridfa_batch_get_stats(const ridfa_batch *b, ridfa_batch_stats *out) {
     if (!b || !out) return RIDFA_E_ARG;
     std::memset(out, 0, sizeof(*out));
-    out->total_bytes = b->total_bytes;
-    out->total_chunks = b->total_chunks;
-    out->n_programs = static_cast<uint32_t>(b->progs.size());
-    out->n_launches = static_cast<uint32_t>(b->groups.size()) + (b->n_segs ? 1 : 0);
-    out->n_tasks = b->n_tasks;
-    out->n_segments = b->n_segs;
+    const ridfa::PlanStats s = ridfa::plan_stats(b->plan);
+    out->total_bytes = s.total_bytes;
+    out->total_chunks = s.total_chunks;
+    out->n_programs = s.n_programs;
+    out->n_launches = s.n_launches;
+    out->n_tasks = s.n_tasks;
+    out->n_segments = s.n_segments;
     out->chunk_len = b->chunk_len;
     out->graph = b->exec ? 1 : 0;
     out->device_bytes = b->dbytes;
@@ -891,6 +953,7 @@ extern "C" void ridfa_batch_free(ridfa_batch *b) {
     cudaSetDevice(b->device);
     cudaDeviceSynchronize();
     ridfa::batch_release(b);
+    ridfa::plan_delete(b->plan);
     cudaSetDevice(cur);
     (void)cudaGetLastError();
     delete b;

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -76,6 +77,20 @@ const DeviceAutomaton *device_copy(const ridfa_program *P, bool dfa, int dev, in
     if (*err != RIDFA_OK) return nullptr;
     vec.push_back(D);
     return &vec.back();
+}
+
+cudaError_t ensure_smem_cap(const void *kern, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> caps;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cap = caps[{kern, dev}];
+    if (bytes <= cap) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+    if (e == cudaSuccess) cap = bytes;
+    return e;
 }
 
 int smem_optin_limit() {
@@ -819,11 +834,8 @@ cudaError_t reach_one(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, 
     using KernT = void (*)(ReachArgs, int, uint32_t);
     KernT kern = PATH == kPathCoop2 ? rid_reach2_kernel<R, LUT, block_cap2<R>()>
                                     : rid_reach_kernel<R, LUT, block_cap<R>(), PATH == kPathCoop2 ? kPathGlobal : PATH>;
-    if (pl.smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(pl.smem));
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = ensure_smem_cap(reinterpret_cast<const void *>(kern), pl.smem);
+    if (e != cudaSuccess) return e;
     if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, pl.block, pl.smem);
     kern<<<pl.grid, pl.block, pl.smem, st>>>(a, pl.tis, pl.staging_offset);
     return cudaGetLastError();

@@ -92,6 +92,9 @@ int cuda_fail(cudaError_t e);
 int upload(const HostAutomaton &H, DeviceAutomaton &D, int dev);
 const DeviceAutomaton *device_copy(const ridfa_program *P, bool dfa, int dev, int *err);
 int smem_optin_limit();
+// Raise a kernel's dynamic shared-memory cap on the current device to at least `bytes`.  The cap
+// is never lowered, so a launch sized by another thread (or an earlier plan) stays valid.
+cudaError_t ensure_smem_cap(const void *kern, size_t bytes);
 
 constexpr uint32_t kMaxJoinBlocks = 1024;
 constexpr uint32_t kPartialWords = 33;

@@ -1,0 +1,148 @@
+"""GPU served recognition: every request's accept bit equals the oracle's (Thompson simulation),
+whether it ran alone or batched with others (continuous batching over several launch slots),
+for host texts copied into the arena and device texts read in place; admission limits."""
+import time
+
+import numpy as np
+import pytest
+
+import textgen
+from oracle.recognizer import SerialRecognizer
+
+pytestmark = pytest.mark.gpu
+
+lib = pytest.importorskip("paper_2412_14975_gb300")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+_XS, _YS = "ABCDEFGHIJKLMNOPQRSTUVWXYZ0123456789!#%&", "bcdefghijklmnopqrstuvwxyz<>=;:@$'\"^_`~,/"
+RES = [textgen.C1_RE, textgen.C3_RE, textgen.C2_RE.replace("{20,60}", "{2,4}"), textgen.regexp_family_re(3),
+       "(" + "|".join(f"{x}a*{y}" for x, y in zip(_XS, _YS)) + ")*"]
+
+
+def make_text(r, n, rng):
+    if r == 0:
+        return textgen.c1_text(n, rng)[:n]
+    if r == 1:
+        return textgen.c3_text(n, rng)[:n]
+    if r == 2:
+        return textgen.c2_text(n, rng)
+    if r == 3:
+        return textgen.regexp_family_text(n, rng)
+    parts, tot = [], 0
+    while tot < n:
+        i = int(rng.integers(len(_XS)))
+        s = _XS[i] + "a" * int(rng.integers(0, 300)) + _YS[i]
+        parts.append(s)
+        tot += len(s)
+    return np.frombuffer("".join(parts).encode(), dtype=np.uint8)[:n]
+
+
+def workload(seed, n):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        r = i % len(RES)
+        ln = int(rng.choice([0, 1, 17, 900, 5000, 40_000, 150_000]))
+        x = make_text(r, ln, rng) if ln else np.zeros(0, np.uint8)
+        if ln > 50 and rng.random() < 0.5:
+            x, _ = textgen.mutate(x, rng, n_subs=1)
+        out.append((r, np.ascontiguousarray(x, dtype=np.uint8)))
+    return out
+
+
+_SER = {}
+
+
+def want(r, x):
+    if r not in _SER:
+        _SER[r] = SerialRecognizer(RES[r])
+    return _SER[r].accepts(x)
+
+
+def collect(srv, n, timeout=60.0):
+    got = {}
+    t0 = time.time()
+    while len(got) < n and time.time() - t0 < timeout:
+        for rid, st, acc, lat in srv.poll(wait_us=2000):
+            assert st == 0, (rid, st)
+            assert lat >= 0.0
+            got[rid] = acc
+    return got
+
+
+def test_served_alone_and_in_the_mix():
+    work = workload(5, 120)
+    expect = [want(r, x) for r, x in work]
+    progs = [lib.ridfa_compile(r) for r in RES]
+    with lib.Server(n_streams=3, arena_bytes=8 << 20, max_batch_requests=40, chunk_len=4096) as srv:
+        slots = [srv.add_program(p) for p in progs]
+        # alone: one request at a time
+        for (r, x), w in list(zip(work, expect))[:30]:
+            rid = srv.submit(slots[r], x)
+            srv.drain()
+            res = srv.poll()
+            assert [(a, b) for a, _, b, _ in res] == [(rid, w)]
+        # in the mix: everything at once (retrying when the 8 MiB arena is full)
+        ids = {}
+        got = {}
+        for j, (r, x) in enumerate(work):
+            while True:
+                rid = srv.try_submit(slots[r], x)
+                if rid is not None:
+                    break
+                for a, st, acc, _ in srv.poll(wait_us=1000):
+                    assert st == 0
+                    got[a] = acc
+            ids[rid] = j
+        srv.drain()
+        got.update(collect(srv, len(work) - len(got)))
+        assert len(got) == len(work)
+        for rid, j in ids.items():
+            assert got[rid] == expect[j], (j, work[j][0], work[j][1].size)
+        st = srv.stats()
+        assert st["completed"] == 30 + len(work)
+        assert st["max_batch"] > 1                 # requests did share batches
+        assert st["n_programs"] == len(RES)
+
+
+def test_served_device_texts_and_admission():
+    work = workload(6, 40)
+    progs = [lib.ridfa_compile(r) for r in RES]
+    with lib.Server(n_streams=2, arena_bytes=1 << 20, max_requests=64, chunk_len=2048) as srv:
+        slots = [srv.add_program(p) for p in progs]
+        # device texts, read in place, some of them unaligned
+        base = torch.zeros(sum(x.size + 21 for _, x in work) + 16, dtype=torch.uint8, device="cuda:0")
+        pos, ids = 0, {}
+        for j, (r, x) in enumerate(work):
+            pos += 5 if j % 3 == 1 else 0
+            if x.size:
+                base[pos:pos + x.size] = torch.from_numpy(x).to("cuda:0")
+            ids[srv.submit(slots[r], base.data_ptr() + pos, length=x.size, device=True)] = j
+            pos = (pos + x.size + 15) & ~15
+        torch.cuda.synchronize()
+        srv.drain()
+        got = collect(srv, len(work))
+        for rid, j in ids.items():
+            assert got[rid] == want(*work[j])
+        # a host text larger than the 1 MiB arena cannot be admitted at all
+        with pytest.raises(lib.RidfaError) as e:
+            srv.submit(slots[1], np.zeros((1 << 20) + 1, np.uint8))
+        assert e.value.code == -12
+        with pytest.raises(lib.RidfaError) as e:
+            srv.submit(len(RES), b"ACGT")
+        assert e.value.code == -1
+        # the request budget: 64 admitted and unpolled at most
+        x = np.frombuffer(b"AGTC" * 4, dtype=np.uint8)
+        n_ok = 0
+        while srv.try_submit(slots[0], x) is not None:
+            n_ok += 1
+            assert n_ok <= 64
+        assert n_ok == 64
+        srv.drain()
+        got = collect(srv, 64)
+        assert len(got) == 64 and all(got.values())
+        assert srv.try_submit(slots[0], x) is not None     # room again after polling
+        srv.drain()
+        assert len(collect(srv, 1)) == 1
