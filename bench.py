@@ -530,6 +530,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dfa", action="store_true")
+    ap.add_argument("--no-counts", action="store_true", help="skip the host transition counters")
     ap.add_argument("--table-mode", type=int, default=0,
                     help="reach-kernel table layout (0 auto, 1 compact, 2 rep16, 3 rep32)")
     ap.add_argument("--text-path", type=int, default=0,
@@ -689,7 +690,28 @@ def main():
         dt = time.perf_counter() - t0
         e2e = {"value": round(n * k / dt / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": n,
                "d2h_bytes_per_step": 1}
-        del h_text, d_in
+        del d_in
+
+    # work of the timed configuration, counted on the host by the library's counter tool:
+    # W_conv (lookups with merged runs, the kernel's algorithmic work) and the paper's W_paper,
+    # for the RID and for the all-states DFA (the transition ratio of the paper's Table 3)
+    work = None
+    if rank == 0 and not args.no_counts:
+        hx = h_text.numpy() if not args.no_e2e else d_text.cpu().numpy()
+        t0 = time.perf_counter()
+        rc = lib.ridfa_count_transitions(prog, hx, c)
+        work = {"rid_w_conv_per_byte": round(rc["w_conv"] / n, 5),
+                "rid_w_paper_per_byte": round(rc["w_paper"] / n, 5),
+                "rid_runs": rc["runs"], "rid_dead_runs": rc["dead_runs"]}
+        if info["n_dfa_states"]:
+            dc = lib.ridfa_count_transitions(prog, hx, c, dfa=True)
+            work.update({"dfa_w_conv_per_byte": round(dc["w_conv"] / n, 5),
+                         "dfa_w_paper_per_byte": round(dc["w_paper"] / n, 5),
+                         "transition_ratio_dfa_over_rid": round(dc["w_paper"] / max(rc["w_paper"], 1), 4)})
+        work["count_s"] = round(time.perf_counter() - t0, 2)
+        roofline["smem_gather"]["lookups_per_byte"] = round(1 + rc["w_conv"] / n, 5)
+    if not args.no_e2e:
+        del h_text
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -708,7 +730,7 @@ def main():
                            "chunk_autotune_GBps": autotune,
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "dfa_value": round(dfa_value, 3) if dfa_value else None,
-                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "work": work,
                 "gpu_launches": 2 * args.steps}
         print(json.dumps(line), flush=True)
     if world > 1:

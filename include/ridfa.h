@@ -136,6 +136,52 @@ int ridfa_delegates(const ridfa_program *prog, uint32_t *out);
 int ridfa_export_tables(const ridfa_program *prog, int which, uint16_t *trans,
                         uint8_t *classmap, uint8_t *final_flags);
 
+/* ---- Sharded recognition (one text split into contiguous shards, e.g. one per GPU).
+ * The join (Sec. 3.2) composes chunk relations associatively, so a shard -- a run of whole
+ * chunks -- reduces to one relation: entered through interface slot a, its chunks lead to a set
+ * of states at its end.  ridfa_recognize_shard computes that summary on the device (reach +
+ * join over the shard's chunks); ridfa_join_shards composes the summaries of consecutive shards
+ * on the host, entering shard j+1 through if_min of the states shard j ends in, and tests the
+ * final set against F^RID.  Only the summaries (a few KB each) cross between shards. */
+typedef struct {
+    uint32_t k;                                   /* interface slots of the program */
+    uint32_t n_out;                               /* distinct states the shard's last chunk ends in */
+    uint16_t entry[RIDFA_MAX_SLOTS];              /* state after the shard's first chunk from slot a
+                                                     (RIDFA_UNDEF: the run dies) */
+    uint16_t out_state[RIDFA_MAX_SLOTS];          /* those end states, ascending */
+    uint32_t reach[RIDFA_MAX_SLOTS][RIDFA_MAX_SLOTS / 32]; /* bit y of row a: entering through slot
+                                                     a can end in out_state[y] */
+} ridfa_shard_summary;
+
+/* Summary of the shard d_text[0, len) cut into n_chunks chunks (1 <= n_chunks <= len), written
+ * to the host struct *h_out; synchronises `stream`.  Errors: as ridfa_recognize. */
+int ridfa_recognize_shard(const ridfa_program *prog, const uint8_t *d_text, size_t len, uint32_t n_chunks,
+                          const ridfa_tuning *tuning, ridfa_shard_summary *h_out, void *stream);
+
+/* Accept bit of the text made of n_shards consecutive shards (the first one starts the text),
+ * from their summaries; host only.  Errors: E_ARG (NULL, n_shards == 0, a summary of another
+ * program's k). */
+int ridfa_join_shards(const ridfa_program *prog, const ridfa_shard_summary *shards, uint32_t n_shards,
+                      uint8_t *h_accept);
+
+/* Transition counts of the reach phase, computed on the host (diagnostics).
+ * Chunk 1 runs from {q0}'s slot only, every other chunk from every interface slot (Sec. 3.2);
+ * which = 1 counts the all-states DFA comparator instead (chunk 1 from q0, the others from
+ * every state of the minimal DFA, Sec. 2). */
+typedef struct {
+    uint64_t w_paper;   /* transitions with every run followed on its own, undefined moves not
+                           counted: the paper's measure (Sec. 1, Fig. 1) */
+    uint64_t w_conv;    /* table lookups when runs in the same state at the same position are
+                           merged: distinct live states summed over positions */
+    uint64_t runs;      /* runs started: 1 + (n_chunks - 1) * k */
+    uint64_t dead_runs; /* runs that met the undefined move before their chunk end */
+} ridfa_transition_counts;
+
+/* h_text: host pointer to len bytes; 1 <= n_chunks <= len; n_threads host threads over the
+ * chunks (0 = all hardware threads).  Errors: E_ARG, E_NO_DFA, E_CHUNKS, E_NOMEM. */
+int ridfa_count_transitions(const ridfa_program *prog, int which, const uint8_t *h_text, size_t len,
+                            uint32_t n_chunks, uint32_t n_threads, ridfa_transition_counts *out);
+
 /* Recognize one text resident on the device (the RID: reach + join, Sec. 3.2).
  * d_text: device pointer to len bytes (any alignment).  n_chunks: c, 1 <= c <= len.
  * len == 0 is allowed with n_chunks == 0: the answer is whether the empty word is in L.

@@ -490,3 +490,61 @@ class Server:
         if not self.handle:
             raise ValueError("server is closed")
         return self.handle
+
+
+# ------------------------------------------------------------------------------ diagnostics
+class TransitionCounts(_c.Structure):
+    _fields_ = [("w_paper", _c.c_uint64), ("w_conv", _c.c_uint64), ("runs", _c.c_uint64),
+                ("dead_runs", _c.c_uint64)]
+
+
+_decl("ridfa_count_transitions", _c.c_int, [_vp, _c.c_int, _vp, _c.c_size_t, _u32, _u32,
+                                            _c.POINTER(TransitionCounts)])
+
+
+def ridfa_count_transitions(prog, text, n_chunks, dfa=False, n_threads=0):
+    """Host transition counts of the reach phase over a host text (bytes or uint8 array):
+    dict with w_paper, w_conv, runs, dead_runs."""
+    if isinstance(text, (bytes, bytearray)):
+        buf = np.frombuffer(text, dtype=np.uint8)
+    else:
+        buf = np.ascontiguousarray(text, dtype=np.uint8)
+    out = TransitionCounts()
+    _check(_lib.ridfa_count_transitions(prog, int(bool(dfa)), buf.ctypes.data if buf.size else None, buf.size,
+                                        int(n_chunks), int(n_threads), _c.byref(out)), "ridfa_count_transitions")
+    return {f: getattr(out, f) for f, _ in out._fields_}
+
+
+# ---------------------------------------------------------------------------------- shards
+class ShardSummary(_c.Structure):
+    _fields_ = [("k", _u32), ("n_out", _u32), ("entry", _c.c_uint16 * RIDFA_MAX_SLOTS),
+                ("out_state", _c.c_uint16 * RIDFA_MAX_SLOTS),
+                ("reach", (_u32 * (RIDFA_MAX_SLOTS // 32)) * RIDFA_MAX_SLOTS)]
+
+    def to_bytes(self):
+        return bytes(self)
+
+    @classmethod
+    def from_bytes(cls, b):
+        return cls.from_buffer_copy(bytes(b))
+
+
+_decl("ridfa_recognize_shard", _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _c.POINTER(Tuning),
+                                          _c.POINTER(ShardSummary), _vp])
+_decl("ridfa_join_shards", _c.c_int, [_vp, _c.POINTER(ShardSummary), _u32, _c.POINTER(_c.c_uint8)])
+
+
+def ridfa_recognize_shard(prog, d_text, length, n_chunks, tuning=None, stream=None):
+    """Relation summary of one shard of a text (device pointer / tensor), as a ShardSummary."""
+    out = ShardSummary()
+    _check(_lib.ridfa_recognize_shard(prog, _ptr(d_text), int(length), int(n_chunks), _tuning(tuning),
+                                      _c.byref(out), _stream(stream)), "ridfa_recognize_shard")
+    return out
+
+
+def ridfa_join_shards(prog, summaries):
+    """Accept bit of the text made of consecutive shards, from their summaries (host only)."""
+    arr = (ShardSummary * len(summaries))(*summaries)
+    acc = _c.c_uint8(0)
+    _check(_lib.ridfa_join_shards(prog, arr, len(summaries), _c.byref(acc)), "ridfa_join_shards")
+    return bool(acc.value)

@@ -536,6 +536,7 @@ struct JoinArgs {
     uint32_t *ticket;
     uint8_t *accept;
     uint32_t per_thread;      // boundaries per thread
+    ridfa_shard_summary *summary;   // non-null: write the shard's relation instead of accept
 };
 
 // Distinct defined values of lambda_i, ascending (at most kMaxD; caller checked m <= kMaxD).
@@ -616,6 +617,116 @@ __device__ bool is_final(const Automaton &A, uint32_t s) {
     return s < A.n && ((A.final_bits[s >> 5] >> (s & 31)) & 1);
 }
 
+// Shard summary when some chunk has more than kMaxD distinct end states (block 0 alone):
+// for every distinct state x the shard's first chunk ends in, propagate if_min({x}) chunk by
+// chunk and record the end states reached, as bits over the last chunk's distinct end states.
+__device__ void summary_wide(const JoinArgs &p, uint32_t *s_vec, uint32_t *s_nvec) {
+    const Automaton &A = p.A;
+    const uint32_t tid = threadIdx.x;
+    ridfa_shard_summary *S = p.summary;
+    __shared__ uint16_t s_out[RIDFA_MAX_SLOTS];
+    __shared__ uint32_t s_nout, s_bits[RIDFA_MAX_SLOTS / 32];
+    const uint16_t *row0 = p.maps;
+    const uint16_t *last = p.maps + static_cast<uint64_t>(p.c - 1) * A.k;
+    if (tid == 0) {
+        // distinct defined end states of the last chunk, ascending
+        uint32_t n = 0;
+        for (uint32_t a = 0; a < A.k; ++a) {
+            const uint16_t v = last[a];
+            if (v == kUndef) continue;
+            uint32_t j = 0;
+            while (j < n && s_out[j] < v) ++j;
+            if (j < n && s_out[j] == v) continue;
+            for (uint32_t t = n; t > j; --t) s_out[t] = s_out[t - 1];
+            s_out[j] = v;
+            ++n;
+        }
+        s_nout = n;
+        S->k = A.k;
+        S->n_out = n;
+    }
+    __syncthreads();
+    for (uint32_t a = tid; a < RIDFA_MAX_SLOTS; a += blockDim.x) {
+        S->out_state[a] = a < s_nout ? s_out[a] : kUndef;
+        S->entry[a] = a < A.k ? row0[a] : kUndef;
+        for (uint32_t w = 0; w < RIDFA_MAX_SLOTS / 32; ++w) S->reach[a][w] = 0;
+    }
+    __syncthreads();
+    for (uint32_t a0 = 0; a0 < A.k; ++a0) {
+        const uint16_t x = row0[a0];
+        if (x == kUndef) continue;
+        bool seen = false;                    // handled with an earlier slot of the same state
+        for (uint32_t b = 0; b < a0 && !seen; ++b) seen = row0[b] == x;
+        if (seen) continue;
+        if (tid < RIDFA_MAX_SLOTS / 32) s_bits[tid] = 0;
+        __syncthreads();
+        if (p.c == 1) {
+            if (tid == 0)
+                for (uint32_t y = 0; y < s_nout; ++y)
+                    if (s_out[y] == x) s_bits[y >> 5] |= 1u << (y & 31);
+        } else {
+            for (uint32_t w = tid; w < A.kw; w += blockDim.x) s_vec[w] = A.ifmask[static_cast<uint64_t>(x) * A.kw + w];
+            __syncthreads();
+            for (uint32_t i = 1; i + 1 < p.c; ++i) {
+                for (uint32_t w = tid; w < A.kw; w += blockDim.x) s_nvec[w] = 0;
+                __syncthreads();
+                const uint16_t *row = p.maps + static_cast<uint64_t>(i) * A.k;
+                for (uint32_t a = tid; a < A.k; a += blockDim.x) {
+                    if (!((s_vec[a >> 5] >> (a & 31)) & 1)) continue;
+                    const uint16_t v = row[a];
+                    if (v == kUndef) continue;
+                    for (uint32_t w = 0; w < A.kw; ++w) {
+                        const uint32_t m = A.ifmask[static_cast<uint64_t>(v) * A.kw + w];
+                        if (m) atomicOr(&s_nvec[w], m);
+                    }
+                }
+                __syncthreads();
+                for (uint32_t w = tid; w < A.kw; w += blockDim.x) s_vec[w] = s_nvec[w];
+                __syncthreads();
+            }
+            for (uint32_t a = tid; a < A.k; a += blockDim.x) {
+                if (!((s_vec[a >> 5] >> (a & 31)) & 1) || last[a] == kUndef) continue;
+                for (uint32_t y = 0; y < s_nout; ++y)
+                    if (s_out[y] == last[a]) atomicOr(&s_bits[y >> 5], 1u << (y & 31));
+            }
+        }
+        __syncthreads();
+        for (uint32_t a = tid; a < A.k; a += blockDim.x)
+            if (row0[a] == x)
+                for (uint32_t w = 0; w < RIDFA_MAX_SLOTS / 32; ++w) S->reach[a][w] = s_bits[w];
+        __syncthreads();
+    }
+}
+
+// Shard summary from the chain product (thread 0 of the last block): tot maps the first chunk's
+// distinct end states D_1 to the last chunk's D_c.
+__device__ void summary_matrix(const JoinArgs &p, const Prod &tot) {
+    const Automaton &A = p.A;
+    ridfa_shard_summary *S = p.summary;
+    uint16_t D0[kMaxD], Dl[kMaxD];
+    const uint32_t m0 = distinct_of(p, 0, D0);
+    const uint32_t ml = distinct_of(p, p.c - 1, Dl);
+    if (m0 == 0xFFFFFFFFu || ml == 0xFFFFFFFFu || (p.c > 1 && tot.nrows == 0xFFFFFFFFu)) {
+        atomicOr(p.status, kStatusBad);
+        return;
+    }
+    S->k = A.k;
+    S->n_out = ml;
+    for (uint32_t y = 0; y < RIDFA_MAX_SLOTS; ++y) S->out_state[y] = y < ml ? Dl[y] : kUndef;
+    for (uint32_t a = 0; a < RIDFA_MAX_SLOTS; ++a) {
+        const uint16_t x = a < A.k ? p.maps[a] : kUndef;
+        S->entry[a] = x;
+        uint32_t bits = 0;
+        if (x != kUndef) {
+            const uint32_t xi = index_of(D0, m0, x);
+            if (xi == 0xFFFFFFFFu) atomicOr(p.status, kStatusBad);
+            else bits = p.c == 1 ? (1u << xi) : tot.rows[xi];
+        }
+        S->reach[a][0] = bits;
+        for (uint32_t w = 1; w < RIDFA_MAX_SLOTS / 32; ++w) S->reach[a][w] = 0;
+    }
+}
+
 __global__ void __launch_bounds__(kJoinThreads) rid_join_kernel(JoinArgs p) {
     __shared__ Prod s_prod[kJoinThreads];
     __shared__ bool s_last;
@@ -627,6 +738,10 @@ __global__ void __launch_bounds__(kJoinThreads) rid_join_kernel(JoinArgs p) {
     if (status0 & kStatusWide) {
         // some chunk has more than kMaxD distinct end states: block 0 propagates if(PLAS_i)
         if (blockIdx.x != 0) return;
+        if (p.summary) {
+            summary_wide(p, s_vec, s_nvec);
+            return;
+        }
         const uint16_t *row0 = p.maps;
         const uint16_t v0 = row0[A.q0_slot];
         if (p.c == 1 || v0 == kUndef) {
@@ -737,6 +852,10 @@ __global__ void __launch_bounds__(kJoinThreads) rid_join_kernel(JoinArgs p) {
     }
     if (tid != 0) return;
     *p.ticket = 0;   // ready for the next launch on this scratch
+    if (p.summary) {
+        summary_matrix(p, tot);
+        return;
+    }
     const uint16_t v0 = p.maps[A.q0_slot];
     uint8_t acc = 0;
     if (v0 != kUndef) {
@@ -760,7 +879,8 @@ __global__ void __launch_bounds__(kJoinThreads) rid_join_kernel(JoinArgs p) {
 }
 
 struct Layout {   // scratch layout for one call
-    size_t maps_off, dinfo_off, partials_off, ticket_off, status_off, accept_off, runs_off, finals_off, total;
+    size_t maps_off, dinfo_off, partials_off, ticket_off, status_off, accept_off, runs_off, finals_off,
+        summary_off, total;
 };
 
 Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks, uint64_t grid_warps) {
@@ -774,6 +894,7 @@ Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks, 
     L.dinfo_off = off; off += al(c * 4);
     L.runs_off = off; off += al(grid_warps * kRunsPerWarp * sizeof(RunEntry));
     L.finals_off = off; off += al(grid_warps * kFinalsPerWarp * 4);
+    L.summary_off = off; off += al(sizeof(ridfa_shard_summary));
     L.maps_off = off; off += need_maps ? al(c * k * 2) : 0;
     L.total = off;
     return L;
@@ -946,7 +1067,8 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
 
 int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, size_t len,
                    uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *d_accept_user,
-                   uint8_t *h_accept, uint16_t *d_maps_user, cudaStream_t st) {
+                   uint8_t *h_accept, uint16_t *d_maps_user, cudaStream_t st,
+                   ridfa_shard_summary *h_summary = nullptr) {
     if (!P) return RIDFA_E_ARG;
     if (use_dfa && !P->has_dfa) return RIDFA_E_NO_DFA;
     const HostAutomaton &H = use_dfa ? P->dfa : P->rid;
@@ -1031,10 +1153,21 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     if (prof) cudaEventRecord(static_cast<cudaEvent_t>(S->ev[1]), st);
 
     // ---- join
-    JoinArgs ja{A, n_chunks, maps, dinfo, status, partials, ticket, accept, per_thread};
+    ridfa_shard_summary *d_summary =
+        h_summary ? reinterpret_cast<ridfa_shard_summary *>(base + L.summary_off) : nullptr;
+    JoinArgs ja{A, n_chunks, maps, dinfo, status, partials, ticket, accept, per_thread, d_summary};
     rid_join_kernel<<<join_blocks, kJoinThreads, 0, st>>>(ja);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
+    if (h_summary) {
+        e = cudaMemcpyAsync(h_summary, d_summary, sizeof(ridfa_shard_summary), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(S->h_status_pinned, status, 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (*S->h_status_pinned & kStatusTimeout) return RIDFA_E_TIMEOUT;
+        if (*S->h_status_pinned & kStatusBad) return RIDFA_E_STATE;
+        return RIDFA_OK;
+    }
     if (prof) {
         cudaEventRecord(static_cast<cudaEvent_t>(S->ev[2]), st);
         S->profiled = true;
@@ -1139,6 +1272,14 @@ extern "C" int ridfa_recognize_dfa_async(const ridfa_program *prog, const uint8_
     if (!d_accept) return RIDFA_E_ARG;
     return ridfa::recognize_impl(prog, true, d_text, len, n_chunks, tuning, d_accept, nullptr,
                                  d_chunk_maps, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ridfa_recognize_shard(const ridfa_program *prog, const uint8_t *d_text, size_t len,
+                                     uint32_t n_chunks, const ridfa_tuning *tuning, ridfa_shard_summary *h_out,
+                                     void *stream) {
+    if (!h_out || len == 0) return RIDFA_E_ARG;
+    return ridfa::recognize_impl(prog, false, d_text, len, n_chunks, tuning, nullptr, nullptr, nullptr,
+                                 static_cast<cudaStream_t>(stream), h_out);
 }
 
 extern "C" int ridfa_last_status(const ridfa_program *prog, void *stream) {

@@ -1,0 +1,126 @@
+"""The library's host transition counters (ridfa_count_transitions) against the oracle.
+
+w_paper is pinned to the oracle's transition_count / csdpa_dfa_transition_count, which the
+paper's worked examples pin (Fig. 1: 9 RID and 15 DFA transitions; Fig. 5: 12 and 9); w_conv is
+checked against its definition -- distinct live states summed over positions -- evaluated here
+with the oracle's RI-DFA and minimal DFA, and both against closed forms on small cases."""
+import numpy as np
+import pytest
+
+import textgen
+from oracle.recognizer import RidOracle
+from oracle.ridfa_sets import (UNDEF, chunk_boundaries, csdpa_dfa_transition_count,
+                               transition_count)
+
+lib = pytest.importorskip("paper_2412_14975_gb300")
+
+
+def w_conv_rid(B, chunks):
+    total = 0
+    for i, y in enumerate(chunks):
+        live = {B.slots[B.delegate[B.nfa.q0]]} if i == 0 else set(B.slots[a] for a in range(B.k))
+        for b in y:
+            total += len(live)
+            live = {p for p in (B.step(s, b) for s in live) if p is not UNDEF}
+            if not live:
+                break
+    return total
+
+
+def w_conv_dfa(d, chunks):
+    total = 0
+    for i, y in enumerate(chunks):
+        live = {d.start} if i == 0 else set(range(len(d.states)))
+        for b in y:
+            total += len(live)
+            live = {p for p in (d.step(s, b) for s in live) if p is not UNDEF}
+            if not live:
+                break
+    return total
+
+
+def chunks_of(x, c):
+    b = chunk_boundaries(len(x), c)
+    return [bytes(x[b[i]:b[i + 1]]) for i in range(c)]
+
+
+def compare(re_src, x, c, n_threads=0):
+    o = RidOracle(re_src)
+    p = lib.ridfa_compile(re_src)
+    ch = chunks_of(x, c)
+    got = lib.ridfa_count_transitions(p, x, c, n_threads=n_threads)
+    assert got["w_paper"] == transition_count(o.B, ch), (re_src, c)
+    assert got["w_conv"] == w_conv_rid(o.B, ch), (re_src, c)
+    assert got["runs"] == 1 + (c - 1) * o.B.k
+    dg = lib.ridfa_count_transitions(p, x, c, dfa=True, n_threads=n_threads)
+    assert dg["w_paper"] == csdpa_dfa_transition_count(o.dfa, ch), (re_src, c)
+    assert dg["w_conv"] == w_conv_dfa(o.dfa, ch), (re_src, c)
+    assert dg["runs"] == 1 + (c - 1) * len(o.dfa.states)
+    return got, dg
+
+
+def test_closed_forms_single_chunk_and_dead_runs():
+    # one chunk: one run from {q0}; (ab)* over "abab" makes 4 transitions and 4 lookups
+    got, dg = compare("(ab)*", b"abab", 1)
+    assert got["w_paper"] == got["w_conv"] == 4 and got["dead_runs"] == 0
+    # a byte outside the alphabet kills every run: no transitions, one lookup per live state
+    p = lib.ridfa_compile("(ab)*")
+    r = lib.ridfa_count_transitions(p, b"zab", 1)
+    assert r == {"w_paper": 0, "w_conv": 1, "runs": 1, "dead_runs": 1}
+    # c = len: every chunk one byte; chunk 1 from {q0}, the others from each of the k slots
+    k = p.info["k"]
+    r = lib.ridfa_count_transitions(p, b"abab", 4)
+    assert r["runs"] == 1 + 3 * k
+
+
+@pytest.mark.parametrize("re_name", ["c1", "c3", "c2_2_4", "regexp3"])
+def test_workload_res_against_oracle(re_name):
+    rng = np.random.Generator(np.random.PCG64(sum(map(ord, re_name))))
+    re_src = {"c1": textgen.C1_RE, "c3": textgen.C3_RE, "c2_2_4": textgen.C2_RE.replace("{20,60}", "{2,4}"),
+              "regexp3": textgen.regexp_family_re(3)}[re_name]
+    n = 3000
+    if re_name == "c1":
+        x = textgen.c1_text(n, rng)[:n]
+    elif re_name == "c3":
+        x = textgen.c3_text(n, rng)[:n]
+    elif re_name == "c2_2_4":
+        x = textgen.c2_text(n, rng)
+    else:
+        x = textgen.regexp_family_text(n, rng)
+    for c in (1, 7, 64):
+        compare(re_src, x, c, n_threads=3)
+
+
+def test_random_res_and_thread_split_invariance():
+    rng = np.random.Generator(np.random.PCG64(0xC0))
+    done = 0
+    while done < 12:
+        node = textgen.random_re(rng, b"abc", depth=int(rng.integers(2, 5)))
+        re_src = "(" + textgen.render(node) + ")*"
+        try:
+            p = lib.ridfa_compile(re_src)
+        except lib.RidfaError:
+            continue
+        if p.info["n_states"] > 400:
+            continue
+        parts = [textgen.sample_member(node, rng, soft_len=12) for _ in range(40)]
+        x = np.frombuffer(b"".join(parts) or b"a", dtype=np.uint8)
+        if done % 2:
+            x, _ = textgen.mutate(x, rng, n_subs=1, alphabet=b"abc")
+        c = int(rng.integers(1, min(x.size, 40) + 1))
+        compare(re_src, x, c, n_threads=1)
+        # any split of the chunks over threads gives the same counts
+        a = lib.ridfa_count_transitions(p, x, c, n_threads=1)
+        for t in (2, 5, 64):
+            assert lib.ridfa_count_transitions(p, x, c, n_threads=t) == a
+        done += 1
+
+
+def test_counter_errors():
+    p = lib.ridfa_compile("(ab)*", build_dfa=False)
+    with pytest.raises(lib.RidfaError) as e:
+        lib.ridfa_count_transitions(p, b"ab", 3)
+    assert e.value.code == -4
+    with pytest.raises(lib.RidfaError) as e:
+        lib.ridfa_count_transitions(p, b"ab", 1, dfa=True)
+    assert e.value.code == -10
