@@ -709,7 +709,16 @@ def main():
                          "dfa_w_paper_per_byte": round(dc["w_paper"] / n, 5),
                          "transition_ratio_dfa_over_rid": round(dc["w_paper"] / max(rc["w_paper"], 1), 4)})
         work["count_s"] = round(time.perf_counter() - t0, 2)
-        roofline["smem_gather"]["lookups_per_byte"] = round(1 + rc["w_conv"] / n, 5)
+        lpb = 1 + rc["w_conv"] / n
+        roofline["smem_gather"]["lookups_per_byte"] = round(lpb, 5)
+        # the binding roof: the slower of the text at HBM bandwidth and the lookups at the
+        # measured gather rate (the microbenchmark does 2 lookups per byte)
+        lut_text_rate = lut_rate * 2.0 / lpb
+        roofline["smem_gather"]["roof_text_GBps"] = round(lut_text_rate, 1)
+        roofline["smem_gather"]["roof_frac"] = round(text_rate / lut_text_rate, 4)
+        hbm_text_rate = peaks["hbm_gbs"] * n / alg_bytes
+        roofline["binding"] = "smem_lookups" if lut_text_rate < hbm_text_rate else "hbm"
+        roofline["binding_frac"] = round(text_rate / min(lut_text_rate, hbm_text_rate), 4)
     if not args.no_e2e:
         del h_text
 

@@ -353,8 +353,8 @@ __device__ __forceinline__ void run_granule2(const LUT &T, uint32_t &s0, uint32_
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int b = h * 8 + q;
-            c0[q] = T.cls_of((w0[b >> 2] >> (8 * (b & 3))) & 0xFF);
-            c1[q] = T.cls_of((w1[b >> 2] >> (8 * (b & 3))) & 0xFF);
+            c0[q] = T.cls_at(w0[b >> 2], b & 3);
+            c1[q] = T.cls_at(w1[b >> 2], b & 3);
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {

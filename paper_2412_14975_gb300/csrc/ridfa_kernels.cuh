@@ -70,8 +70,8 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
     return v;
 }
 __device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
-    uint16_t v;
-    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    uint32_t v;                       // zero-extended into a 32-bit register: no conversion
+    asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
 __device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
@@ -149,10 +149,13 @@ __device__ __forceinline__ uint4 lds_v4(uint32_t addr) {
     return v;
 }
 __device__ __forceinline__ uint32_t lds_u8(uint32_t addr) {
-    uint16_t v;
-    asm volatile("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(addr));
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
+// Byte q (0..3) of w in the low 8 bits.  Shift and mask run on the integer pipes; a byte permute
+// (PRMT) measured slower here, as it competes with the table lookups for the shared-memory pipe.
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, int q) { return (w >> (8 * q)) & 0xFF; }
 
 // Table lookup policies.  A run's state is kept in the policy's own encoding (`enc`); `id`
 // recovers the automaton state number.
@@ -177,6 +180,7 @@ struct LutPlain {
     __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id; }
     __device__ __forceinline__ uint32_t id(uint32_t s) const { return s; }
     __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return cls[b]; }
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return cls[byte_of(w, q)]; }
     __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return t[s * C + c]; }
 };
 
@@ -230,6 +234,8 @@ struct LutRep {
     __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id * row; }
     __device__ __forceinline__ uint32_t id(uint32_t s) const { return s / row; }
     __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
+    // class of byte q of w
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
     __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const {
         return W16 ? lds_u16(lt + s + c) : lds_u32(lt + s + c);
     }
@@ -458,7 +464,7 @@ __device__ __forceinline__ uint32_t run_granule(const LUT &T, uint32_t s, uint32
     const uint32_t w[4] = {x.x, x.y, x.z, x.w};
     uint32_t cl[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
+    for (int q = 0; q < 16; ++q) cl[q] = T.cls_at(w[q >> 2], q & 3);
 #pragma unroll
     for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
     return s;
@@ -538,7 +544,7 @@ __device__ __forceinline__ void tail_converge(const LUT &T, const uint8_t *t, ui
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
             uint32_t cl[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) cl[q] = T.cls_of((w[q >> 2] >> (8 * (q & 3))) & 0xFF);
+            for (int q = 0; q < 16; ++q) cl[q] = T.cls_at(w[q >> 2], q & 3);
 #pragma unroll
             for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
             pos += 16;
