@@ -125,6 +125,14 @@ class ClockSampler:
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
 
 
+# DRAM bytes (read + write) per text byte of the reach kernel, from the ncu capture summarised in
+# profiles/reach_c3_1GiB_coop_staging.md (record-line RE, 1 GiB, 155,648 chunks); applied to the
+# record-line workload in the same launch shape (Rep16 tables, cooperative staging), scaled by the
+# text bytes.  Must be re-measured (or dropped) whenever that kernel changes.
+REACH_TRAFFIC = {"workload": "c3", "kernel": "rid_reach_kernel<4, LutRep<true>, 1024, 2>",
+                 "dram_bytes_per_text_byte": 1.0311}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -664,8 +672,11 @@ def main():
     # measured on this GPU by the library's microbenchmark
     lut_rate = lib.ridfa_bench_smem_gather(1 << 16) / 1e9
     text_rate = n / (reach_ms / 1e3) / 1e9
+    traffic = None
+    if name == REACH_TRAFFIC["workload"] and args.table_mode == 0 and args.text_path == 0 and c == 155648:
+        traffic = int(REACH_TRAFFIC["dram_bytes_per_text_byte"] * n)
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "kernel": "rid_reach_kernel", "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(reach_ms, 4),
                 "join_ms": round(join_ms, 4),
