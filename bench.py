@@ -125,10 +125,10 @@ class ClockSampler:
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
 
 
-# DRAM bytes (read + write) per text byte of the reach kernel, from the ncu capture summarised in
-# profiles/reach_c3_1GiB_coop_staging.md (record-line RE, 1 GiB, 155,648 chunks); applied to the
-# record-line workload in the same launch shape (Rep16 tables, cooperative staging), scaled by the
-# text bytes.  Must be re-measured (or dropped) whenever that kernel changes.
+# DRAM bytes (read + write) per text byte of the reach kernel, from one ncu capture of it
+# (record-line RE, 1 GiB, 155,648 chunks: dram__bytes_read.sum + dram__bytes_write.sum); applied
+# to the record-line workload in the same launch shape (Rep16 tables, cooperative staging), scaled
+# by the text bytes.  Must be re-measured (or dropped) whenever that kernel changes.
 REACH_TRAFFIC = {"workload": "c3", "kernel": "rid_reach_kernel<4, LutRep<true>, 1024, 2>",
                  "dram_bytes_per_text_byte": 1.0311}
 
