@@ -36,13 +36,18 @@ WORKLOADS = {
     "c3any": ("ASCII record lines, any field per column ((F)(,F)*\\n)*", 4 << 30, 1 << 17),
     "c2": ("DNA motif RE with the {2,4} codon repeat, i.i.d. ACGT", 1 << 30, 1 << 16),
     "c1": ("((A|C)*G(T|A)+C)*, walk on the minimal DFA", 1 << 20, 64),
+    "regexp": ("(a|b)*a(a|b){k}, i.i.d. a/b (the paper's regexp family)", 1 << 30, 1 << 17),
 }
+
+
+REGEXP_K = 7   # (a|b)*a(a|b){7}: the minimal DFA has 256 states (the comparator's limit), k = 9
 
 
 def workload_re(name):
     import textgen
     return {"c3": textgen.C3_RE, "c3any": textgen.C3_RE_ANYFIELD,
-            "c2": textgen.C2_RE.replace("{20,60}", "{2,4}"), "c1": textgen.C1_RE}[name]
+            "c2": textgen.C2_RE.replace("{20,60}", "{2,4}"), "c1": textgen.C1_RE,
+            "regexp": textgen.regexp_family_re(REGEXP_K)}[name]
 
 
 def make_text(name, n, seed, device):
@@ -51,11 +56,12 @@ def make_text(name, n, seed, device):
     import textgen
     if name in ("c3", "c3any"):
         return textgen.c3_text_torch(n, seed, device=device)
-    if name == "c2":
+    if name in ("c2", "regexp"):
         g = torch.Generator(device=device)
         g.manual_seed(seed)
-        lut = torch.tensor(list(b"ACGT"), dtype=torch.uint8, device=device)
-        return lut[torch.randint(0, 4, (n,), generator=g, device=device)]
+        alpha = b"ACGT" if name == "c2" else b"ab"
+        lut = torch.tensor(list(alpha), dtype=torch.uint8, device=device)
+        return lut[torch.randint(0, len(alpha), (n,), generator=g, device=device)]
     x = textgen.c1_text(n, seed)
     return torch.from_numpy(x).to(device)
 
@@ -68,6 +74,8 @@ def sample_text_numpy(name, n, seed):
         return textgen.c3_text(n, seed)
     if name == "c2":
         return textgen.c2_text(n, seed)
+    if name == "regexp":
+        return textgen.regexp_family_text(n, seed)
     return textgen.c1_text(n, seed)
 
 
@@ -454,6 +462,7 @@ def run_served(args, lib, torch, dev, rank):
             pick = rng.integers(0, len(texts), size=n)
             late = {}
             lat = []
+            srv_lat = []
             st0 = srv.stats()
             nbytes = 0
             i = 0
@@ -470,6 +479,7 @@ def run_served(args, lib, torch, dev, rank):
                         continue
                 for r_id, st, acc, us in srv.poll(wait_us=0 if i < n else 1000):
                     lat.append(late.pop(r_id) * 1e3 + us / 1e3)
+                    srv_lat.append(us / 1e3)
             wall = time.perf_counter() - tstart
             st1 = srv.stats()
             lat = np.sort(np.array(lat))
@@ -478,7 +488,9 @@ def run_served(args, lib, torch, dev, rank):
                             "GBps": round(nbytes / wall / 1e9, 3),
                             "p50_ms": round(float(np.percentile(lat, 50)), 3),
                             "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                            "max_ms": round(float(lat[-1]), 3), "batches": nb,
+                            "max_ms": round(float(lat[-1]), 3),
+                            "server_p50_ms": round(float(np.percentile(srv_lat, 50)), 3),
+                            "server_p99_ms": round(float(np.percentile(srv_lat, 99)), 3), "batches": nb,
                             "mean_batch": round(n / max(nb, 1), 1),
                             "busy_retries": st1["rejected"] - st0["rejected"]})
     stats = srv.stats()
@@ -526,7 +538,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["batch", "served"])
-    ap.add_argument("--served-rates", default="2000,5000,10000,20000,50000")
+    ap.add_argument("--served-rates", default="2000,5000,10000,20000,50000,100000,200000")
     ap.add_argument("--served-seconds", type=float, default=5.0)
     ap.add_argument("--served-ref-rate", type=int, default=10000)
     ap.add_argument("--served-pool", type=int, default=2048)
@@ -539,6 +551,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dfa", action="store_true")
     ap.add_argument("--no-counts", action="store_true", help="skip the host transition counters")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time the unminimised interface (every NFA state a slot)")
     ap.add_argument("--table-mode", type=int, default=0,
                     help="reach-kernel table layout (0 auto, 1 compact, 2 rep16, 3 rep32)")
     ap.add_argument("--text-path", type=int, default=0,
@@ -684,6 +698,18 @@ def main():
                                 "frac": round(text_rate / lut_rate, 4),
                                 "note": "ridfa_bench_smem_gather: 2 lane-private gathers per byte, all SMs"}}
 
+    # the effect of interface minimisation (Sec. 3.4): the same text with I^B = every singleton
+    ablation = None
+    if args.ablation:
+        pu = lib.ridfa_compile(re_src, minimize_interface=False, build_dfa=False)
+        if pu.info["k"] <= lib.RIDFA_MAX_SLOTS:
+            def step_unmin():
+                lib.ridfa_recognize_async(pu, d_text, n, c, d_accept, stream=stream)
+            assert lib.ridfa_recognize(pu, d_text, n, c, stream=stream) == acc
+            ums = timed(step_unmin, max(3, args.steps // 2), args.warmup)
+            ablation = {"unminimized_k": pu.info["k"], "minimized_k": info["k"],
+                        "unminimized_GBps": round(world * n * max(3, args.steps // 2) / (ums / 1e3) / 1e9, 3)}
+
     e2e = None
     if not args.no_e2e:
         h_text = torch.empty(n, dtype=torch.uint8, pin_memory=True)
@@ -751,6 +777,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "dfa_value": round(dfa_value, 3) if dfa_value else None,
                 "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "work": work,
+                "interface_ablation": ablation,
                 "gpu_launches": 2 * args.steps}
         print(json.dumps(line), flush=True)
     if world > 1:
