@@ -90,7 +90,8 @@ typedef struct {
                                  call's stream (read them back with ridfa_last_timings) */
     uint32_t table_mode;      /* reach-kernel table layout: 0 auto; 1 compact uint16 table;
                                  2 lane-replicated 16-bit offsets; 3 lane-replicated 32-bit
-                                 offsets (E_ARG if the chosen layout does not fit) */
+                                 offsets; 4 half-replicated (16 copies of the transition table)
+                                 (E_ARG if the chosen layout does not fit) */
     uint32_t text_path;       /* how the converged runs read the text: 0 auto; 1 each lane's own
                                  16-byte global loads; 2 per-lane bulk copies (cp.async.bulk)
                                  into a shared-memory ring; 3 warp-cooperative coalesced loads
@@ -163,6 +164,16 @@ int ridfa_recognize_shard(const ridfa_program *prog, const uint8_t *d_text, size
  * program's k). */
 int ridfa_join_shards(const ridfa_program *prog, const ridfa_shard_summary *shards, uint32_t n_shards,
                       uint8_t *h_accept);
+
+/* Per-chunk join states (the join of Sec. 3.2 as a full scan instead of a reduction), from the
+ * chunk maps of one recognition of `prog` (d_maps: device [n_chunks][k], as written by
+ * ridfa_recognize with d_chunk_maps).  d_entry (device, uint32 [n_chunks][ceil(k/32)], or NULL)
+ * receives, per chunk i, the bit set E_i = if_min(PLAS_{i-1}) ∩ PIS_i of interface slots the
+ * chunk is entered through (E_1 = {q0's slot} ∩ PIS_1), so that PLAS_i = λ_i(E_i); *h_reject
+ * is the first chunk (0-based) whose PLAS_i is empty -- where the text is rejected -- or -1.
+ * Synchronises `stream`.  Errors: E_ARG, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_STATE. */
+int ridfa_join_scan(const ridfa_program *prog, const uint16_t *d_maps, uint32_t n_chunks, uint32_t *d_entry,
+                    int64_t *h_reject, void *stream);
 
 /* Transition counts of the reach phase, computed on the host (diagnostics).
  * Chunk 1 runs from {q0}'s slot only, every other chunk from every interface slot (Sec. 3.2);
@@ -316,7 +327,8 @@ typedef struct {
     uint32_t max_requests;      /* requests admitted and not yet polled; 0 = 1 << 20 */
     uint32_t max_batch_requests;/* requests per batch; 0 = 8192 */
     uint64_t max_batch_bytes;   /* text bytes per batch; 0 = 512 MiB */
-    uint32_t chunk_len;         /* bytes per chunk; 0 = 8192 */
+    uint32_t chunk_len;         /* bytes per chunk; 0 = adapted per batch: about two chunks per
+                                   resident lane of the GPU, a power of two in [1 KiB, 8 KiB] */
     uint32_t reserved;
 } ridfa_server_opts;
 

@@ -18,4 +18,4 @@ from ._lib import (RIDFA_MAX_SLOTS, RIDFA_MAX_STATES, RIDFA_NOALLOC_SCRATCH_BYTE
                    ridfa_slots, ridfa_state_set, ridfa_strerror, chunk_boundaries,
                    Batch, ridfa_batch_create, ridfa_batch_run, ridfa_batch_get_stats, ridfa_batch_free,
                    ridfa_recognize_batch, Server, RIDFA_SUBMIT_DEVICE_TEXT, ridfa_count_transitions,
-                   ShardSummary, ridfa_recognize_shard, ridfa_join_shards)
+                   ShardSummary, ridfa_recognize_shard, ridfa_join_shards, ridfa_join_scan)

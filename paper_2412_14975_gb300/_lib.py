@@ -548,3 +548,16 @@ def ridfa_join_shards(prog, summaries):
     acc = _c.c_uint8(0)
     _check(_lib.ridfa_join_shards(prog, arr, len(summaries), _c.byref(acc)), "ridfa_join_shards")
     return bool(acc.value)
+
+
+# ------------------------------------------------------------------------------ join scan
+_decl("ridfa_join_scan", _c.c_int, [_vp, _vp, _u32, _vp, _c.POINTER(_c.c_int64), _vp])
+
+
+def ridfa_join_scan(prog, d_maps, n_chunks, d_entry=None, stream=None):
+    """Per-chunk entry sets E_i into d_entry (device uint32 [n_chunks][ceil(k/32)], optional);
+    returns the first rejecting chunk or -1."""
+    rej = _c.c_int64(0)
+    _check(_lib.ridfa_join_scan(prog, _ptr(d_maps), int(n_chunks), _ptr(d_entry), _c.byref(rej), _stream(stream)),
+           "ridfa_join_scan")
+    return rej.value

@@ -241,6 +241,48 @@ struct LutRep {
     }
 };
 
+// Half-replicated tables, for transition tables too large to replicate 32 times: the class table
+// as in LutRep (32 copies, conflict-free), the transition table in F = 16 copies, lane l reading
+// copy l & 15.  Entry (s, c) sits at byte ((s * Cp/2 + c/2) * 16 + (l & 15)) * 4 + (c & 1) * 2, so
+// lanes of different copies never share a bank and the two lanes of one copy share one only when
+// their rows differ with the same parity: at most 2 wavefronts per gather.  States are kept in
+// 2-byte units (s * Cp * 16), so a step is one add of a doubled state and the class offset.
+struct LutPart {
+    static constexpr uint32_t F = 16;
+    uint32_t lc, lt;          // shared addresses of this lane's class copy / transition copy
+    uint32_t unit;            // 2-byte units per state row: Cp * F
+    __host__ __device__ static uint32_t cpad(const Automaton &A) { return (A.C + 1) & ~1u; }
+    static size_t smem_bytes(const Automaton &A) {
+        return 256 * 128 + static_cast<size_t>(A.n + 1) * (cpad(A) / 2) * (4 * F);
+    }
+    static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n) * cpad(A) * F <= 0xFFFF; }
+    __device__ __forceinline__ static uint32_t cls_off(uint32_t c) { return (c >> 1) * (4 * F) + (c & 1) * 2; }
+    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+        const uint32_t Cp = cpad(A);
+        unit = Cp * F;
+        const uint32_t base_c = smem_addr(smem);
+        const uint32_t base_t = base_c + 256 * 128;
+        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x)
+            sts_u32(base_c + i * 4, cls_off(A.classmap[i >> 5]));
+        const uint32_t words = (A.n + 1) * (Cp / 2) * F;
+        for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
+            const uint32_t rowp = i / F;                       // s * Cp/2 + c/2
+            const uint32_t s = rowp / (Cp / 2), c0 = 2 * (rowp % (Cp / 2));
+            const uint32_t n0 = A.trans[s * A.C + c0];
+            const uint32_t n1 = (c0 + 1 < A.C) ? A.trans[s * A.C + c0 + 1] : A.n;
+            sts_u32(base_t + i * 4, (n0 * unit) | ((n1 * unit) << 16));
+        }
+        const uint32_t lane = threadIdx.x & 31;
+        lc = base_c + lane * 4;
+        lt = base_t + (lane & (F - 1)) * 4;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id * unit; }
+    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s / unit; }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return lds_u16(lt + 2 * s + c); }
+};
+
 // Chunk-map row of one chunk written by one lane: entries of alive slots get `val`.
 template <int R>
 __device__ __forceinline__ void write_row(uint16_t *row, uint32_t k, const uint32_t (&alive)[R],

@@ -113,8 +113,10 @@ __global__ void __launch_bounds__(kScanThreads) rid_scan_products(ScanArgs p) {
         atomicOr(p.status, kStatusWide);
         return;
     }
+    // rows stay over the segment's first D; the columns move on to each next D
     uint32_t rows[kMaxD];
     for (uint32_t x = 0; x < mp; ++x) rows[x] = 1u << x;
+    uint32_t mcur = mp;
     bool bad = false;
     for (uint64_t i = b0; i < b1; ++i) {
         const uint16_t *row = p.maps + i * A.k;
@@ -123,17 +125,15 @@ __global__ void __launch_bounds__(kScanThreads) rid_scan_products(ScanArgs p) {
             atomicOr(p.status, kStatusWide);
             return;
         }
+        uint32_t M[kMaxD];                       // row z of M_i: D_{i-1}[z] -> bits over D_i
+        for (uint32_t z = 0; z < mcur; ++z) M[z] = step_plas(A, row, Dp, 1u << z, Dc, mc, nullptr, &bad);
         for (uint32_t x = 0; x < mp; ++x) {
             uint32_t out = 0;
-            for (uint32_t bits = rows[x]; bits; bits &= bits - 1) {
-                // row z of M_i: D_{i-1}[z] -> bits over D_i
-                const uint32_t z = __ffs(bits) - 1;
-                out |= step_plas(A, row, Dp, 1u << z, Dc, mc, nullptr, &bad);
-            }
+            for (uint32_t bits = rows[x]; bits; bits &= bits - 1) out |= M[__ffs(bits) - 1];
             rows[x] = out;
         }
         for (uint32_t j = 0; j < mc; ++j) Dp[j] = Dc[j];
-        // the matrix keeps its rows over the segment's first D; only the columns move on
+        mcur = mc;
     }
     if (bad) atomicOr(p.status, kStatusBad);
     P[0] = mp;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kScanThreads) rid_scan_walk(ScanArgs p) {
     const uint64_t b0 = 1 + static_cast<uint64_t>(t) * kScanSeg;
     const uint64_t b1 = b0 + kScanSeg < p.c ? b0 + kScanSeg : p.c;
     uint16_t Dp[kMaxD], Dc[kMaxD];
-    uint32_t mp = row_distinct(p.maps + (b0 - 1) * A.k, A.k, Dp);
+    row_distinct(p.maps + (b0 - 1) * A.k, A.k, Dp);
     uint32_t v = p.vin[t];
     bool bad = false;
     for (uint64_t i = b0; i < b1; ++i) {
@@ -196,9 +196,7 @@ __global__ void __launch_bounds__(kScanThreads) rid_scan_walk(ScanArgs p) {
         if (nv == 0 && v != 0) atomicMin(p.reject, static_cast<unsigned long long>(i));
         v = nv;
         for (uint32_t j = 0; j < mc; ++j) Dp[j] = Dc[j];
-        mp = mc;
     }
-    (void)mp;
     if (bad) atomicOr(p.status, kStatusBad);
 }
 

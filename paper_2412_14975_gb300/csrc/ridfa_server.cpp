@@ -131,6 +131,7 @@ struct Slot {                          // one launch slot: a batch in flight at 
 
 struct ridfa_server {
     int device = 0;
+    int sms = 1;
     ridfa_server_opts o{};
     std::vector<const ridfa_program *> progs;     // guarded by mu; only appended
     uint8_t *darena = nullptr, *harena = nullptr;
@@ -245,10 +246,22 @@ void launch(ridfa_server *S, Slot &sl, std::vector<Request> &batch) {
     }
     flush();
     std::vector<ridfa_batch_item> items(n);
-    for (uint32_t i = 0; i < n; ++i) items[i] = ridfa_batch_item{batch[i].dtext, batch[i].len, batch[i].prog, 0};
+    uint64_t bytes = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        items[i] = ridfa_batch_item{batch[i].dtext, batch[i].len, batch[i].prog, 0};
+        bytes += batch[i].len;
+    }
+    // chunk length: the configured one, else adapted to the batch -- about two chunks per resident
+    // lane of the GPU (short chunks keep a small batch's latency low, long ones cut the
+    // speculation overhead of a large batch), a power of two in [1 KiB, 8 KiB]
+    uint32_t L = S->o.chunk_len;
+    if (L == 0) {
+        const uint64_t per = bytes / (2ull * static_cast<uint64_t>(S->sms) * 1024);
+        L = 1024;
+        while (L < 8192 && L < per) L <<= 1;
+    }
     if (err == RIDFA_OK)
-        err = plan_build(sl.plan, progs.data(), static_cast<uint32_t>(progs.size()), items.data(), n,
-                         S->o.chunk_len, S->device);
+        err = plan_build(sl.plan, progs.data(), static_cast<uint32_t>(progs.size()), items.data(), n, L, S->device);
     if (err == RIDFA_OK) err = grow_slot(S, sl, plan_device_bytes(sl.plan), plan_image_bytes(sl.plan));
     if (err == RIDFA_OK) {
         const size_t img = plan_image_bytes(sl.plan);
@@ -387,11 +400,12 @@ extern "C" int ridfa_server_create(const ridfa_server_opts *opts, ridfa_server *
     if (!o.max_requests) o.max_requests = 1u << 20;
     if (!o.max_batch_requests) o.max_batch_requests = 8192;
     if (!o.max_batch_bytes) o.max_batch_bytes = 512ull << 20;
-    if (!o.chunk_len) o.chunk_len = 8192;
     o.arena_bytes = ridfa::round16(o.arena_bytes);
     S->o = o;
     S->device = o.device;
     ridfa::DeviceGuard g(S->device);
+    cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device);
+    if (S->sms < 1) S->sms = 1;
     int err = RIDFA_OK;
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&S->darena), o.arena_bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&S->harena), o.arena_bytes, cudaHostAllocDefault);

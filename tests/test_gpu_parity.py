@@ -193,10 +193,10 @@ def test_text_paths_agree(path):
             assert np.array_equal(got[i], want[i])
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4])
 def test_tuning_variants_agree(mode):
-    """Every table layout (compact, lane-replicated 16/32-bit) and launch shape gives the same
-    bit-exact maps."""
+    """Every table layout (compact, lane-replicated 16/32-bit, half-replicated) and launch shape
+    gives the same bit-exact maps."""
     x = textgen.c3_text(1 << 18, seed=77)
     for t in [dict(probe_interval=1), dict(probe_interval=64), dict(block_threads=64),
               dict(grid_blocks=1), dict(block_threads=128, grid_blocks=3),
@@ -210,9 +210,10 @@ def test_tuning_variants_agree(mode):
     check(textgen.C1_RE, y, 300, tuning=dict(table_mode=mode))
     re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
     z = textgen.c2_text(1 << 16, seed=79)
-    # 424 states x 5 classes: only the compact layout fits (16-bit offsets overflow, the 32-bit
-    # replicated table exceeds shared memory), so the automatic choice must pick it
-    check(re2, z, 200, tuning=dict(table_mode=1 if mode == 1 else 0), dfa_too=False)
+    # 424 states x 5 classes: the 16-bit offsets overflow and the 32-bit replicated table exceeds
+    # shared memory; the compact table (automatic) and the half-replicated one (on request) fit
+    check(re2, z, 200, tuning=dict(table_mode=mode if mode in (1, 4) else 0), dfa_too=False)
+    check(re2, z, 1000, tuning=dict(table_mode=mode if mode in (1, 4) else 0, text_path=1), dfa_too=False)
     prog = lib.ridfa_compile(re2)
     d = to_device(z)
     for bad in (2, 3):
