@@ -88,9 +88,11 @@ typedef struct {
     uint32_t grid_blocks;     /* reach-kernel blocks: 0 auto (one wave on all SMs) */
     uint32_t profile;         /* 1: record CUDA events around the reach and join launches on the
                                  call's stream (read them back with ridfa_last_timings) */
-    uint32_t table_mode;      /* reach-kernel table layout: 0 auto; 1 compact uint16 table;
-                                 2 lane-replicated 16-bit offsets; 3 lane-replicated 32-bit
-                                 offsets; 4 half-replicated (16 copies of the transition table)
+    uint32_t table_mode;      /* reach-kernel table layout: 0 auto; 1 compact (premultiplied
+                                 16-bit offsets in shared memory, else the uint16 table through
+                                 generic loads); 2 lane-replicated 16-bit offsets; 3
+                                 lane-replicated 32-bit offsets; 4 half-replicated (16 copies of
+                                 the transition table); 5 the uint16 table through generic loads
                                  (E_ARG if the chosen layout does not fit) */
     uint32_t text_path;       /* how the converged runs read the text: 0 auto; 1 each lane's own
                                  16-byte global loads; 2 per-lane bulk copies (cp.async.bulk)

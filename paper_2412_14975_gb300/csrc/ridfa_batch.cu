@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kBatchJoinThreads) rid_join_batch_kernel(Batch
 }
 
 // ---------------------------------------------------------------------------- host side
-enum BMode : uint32_t { kBPlain = 1, kBRep16 = 2, kBRep32 = 3 };
+enum BMode : uint32_t { kBPlain = 1, kBRep16 = 2, kBRep32 = 3, kBFlat = 4 };
 
 struct LaunchGroup {          // one persistent reach launch
     uint32_t mode = kBPlain;
@@ -473,13 +473,15 @@ cudaError_t batch_reach(const LaunchGroup &g, const BatchReachArgs &a, cudaStrea
         switch (g.mode) {
             case kBRep16: return batch_reach_r<LutRep<true>, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
             case kBRep32: return batch_reach_r<LutRep<false>, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-            default: return batch_reach_r<LutPlain, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+            case kBPlain: return batch_reach_r<LutPlain, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+            default: return batch_reach_r<LutFlat, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
         }
     }
     switch (g.mode) {
         case kBRep16: return batch_reach_r<LutRep<true>, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
         case kBRep32: return batch_reach_r<LutRep<false>, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-        default: return batch_reach_r<LutPlain, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+        case kBPlain: return batch_reach_r<LutPlain, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+        default: return batch_reach_r<LutFlat, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
     }
 }
 
@@ -577,11 +579,13 @@ int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, co
         if (!P.dev[p]) return err;
         const HostAutomaton &H = R->rid;
         Automaton A{nullptr, nullptr, nullptr, nullptr, nullptr, H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
-        const size_t r16 = LutRep<true>::smem_bytes(A), r32 = LutRep<false>::smem_bytes(A), pln = LutPlain::smem_bytes(A);
+        const size_t r16 = LutRep<true>::smem_bytes(A), r32 = LutRep<false>::smem_bytes(A),
+                     pln = LutPlain::smem_bytes(A), flt = LutFlat::smem_bytes(A);
         if (LutRep<true>::fits16(A) && r16 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep16; tbytes[p] = r16; }
         else if (r32 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep32; tbytes[p] = r32; }
-        else if (pln + 8 * kWarpCoopBytes <= limit) { mode[p] = kBPlain; P.tis[p] = 1; tbytes[p] = pln; }
-        else { mode[p] = kBPlain; P.tis[p] = 0; tbytes[p] = 256; }
+        else if (LutPlain::fits(A) && pln + 8 * kWarpCoopBytes <= limit) { mode[p] = kBPlain; tbytes[p] = pln; }
+        else if (flt + 8 * kWarpCoopBytes <= limit) { mode[p] = kBFlat; P.tis[p] = 1; tbytes[p] = flt; }
+        else { mode[p] = kBFlat; P.tis[p] = 0; tbytes[p] = 256; }
     }
     // texts grouped by program; chunk counts
     std::vector<std::vector<uint32_t>> by_prog(np);
@@ -613,7 +617,7 @@ int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, co
     P.groups.clear();
     P.tasks.clear();
     uint64_t run_warps = 0;
-    for (uint32_t m = kBPlain; m <= kBRep32; ++m) {
+    for (uint32_t m = kBPlain; m <= kBFlat; ++m) {
         LaunchGroup g;
         g.mode = m;
         g.coop = aligned_all;

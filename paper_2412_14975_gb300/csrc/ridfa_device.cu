@@ -929,7 +929,7 @@ DeviceScratch *scratch_for(const ridfa_program *P, int dev, size_t bytes, int *e
     return S;
 }
 
-enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3, kModePart16 = 4 };
+enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3, kModePart16 = 4, kModeFlat = 5 };
 
 // How one reach launch is laid out: table layout, text path, block/grid, shared memory.
 struct ReachPlan {
@@ -978,7 +978,8 @@ cudaError_t reach_m(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, in
         case kModeRep16: return reach_r<LutRep<true>, PATH>(a, pl, st, per_sm);
         case kModeRep32: return reach_r<LutRep<false>, PATH>(a, pl, st, per_sm);
         case kModePart16: return reach_r<LutPart, PATH>(a, pl, st, per_sm);
-        default: return reach_r<LutPlain, PATH>(a, pl, st, per_sm);
+        case kModePlain: return reach_r<LutPlain, PATH>(a, pl, st, per_sm);
+        default: return reach_r<LutFlat, PATH>(a, pl, st, per_sm);
     }
 }
 
@@ -1006,17 +1007,18 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // (the half-replicated layout is only taken on request: on the codon RE, the one workload it
     // would serve, it measured slower than the compact table -- its gathers conflict less, but
     // its larger footprint leaves fewer warps and the time goes to run imbalance, not conflicts)
+    const size_t plain = LutPlain::smem_bytes(A), flat = LutFlat::smem_bytes(A);
     const bool ok16 = LutRep<true>::fits16(A) && rep16 <= limit, ok32 = rep32 <= limit,
-               okp = LutPart::fits(A) && part16 <= limit;
+               okp = LutPart::fits(A) && part16 <= limit, okplain = LutPlain::fits(A) && plain <= limit;
     if (mode == 0) mode = ok16 ? kModeRep16 : ok32 ? kModeRep32 : kModePlain;
+    if (mode == kModePlain && !okplain) mode = kModeFlat;    // the compact table, through generic loads
     if ((mode == kModeRep16 && !ok16) || (mode == kModeRep32 && !ok32) || (mode == kModePart16 && !okp))
         return RIDFA_E_ARG;
-    if (mode < kModePlain || mode > kModePart16) return RIDFA_E_ARG;
+    if (mode < kModePlain || mode > kModeFlat) return RIDFA_E_ARG;
     pl.mode = mode;
-    const size_t plain_bytes = LutPlain::smem_bytes(A);
-    pl.tis = (mode == kModePlain && plain_bytes <= limit) ? 1 : 0;
+    pl.tis = (mode == kModeFlat && flat <= limit) ? 1 : 0;
     const size_t table_smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : mode == kModePart16 ? part16
-                              : (pl.tis ? plain_bytes : 256);
+                              : mode == kModePlain ? plain : (pl.tis ? flat : 256);
     const int cap = pl.R <= 4 ? 1024 : 512;
     const uint32_t text_path = tuning ? tuning->text_path : 0;
     if (text_path > 4) return RIDFA_E_ARG;
@@ -1049,7 +1051,7 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
                           : pl.path == kPathCoop  ? w_coop
                           : pl.path == kPathCoop2 ? w_coop2
                                                   : cap / 32;
-    if (block == 0) block = pl.path == kPathGlobal ? (mode == kModePlain ? 256 : cap) : warps_fit * 32;
+    if (block == 0) block = pl.path == kPathGlobal ? (mode == kModeFlat && !pl.tis ? 256 : cap) : warps_fit * 32;
     if (block < 32 || block > (pl.path == kPathCoop2 ? cap2 : cap) || block % 32) return RIDFA_E_ARG;
     pl.block = block;
     pl.smem = pl.path == kPathBulk    ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpStageBytes

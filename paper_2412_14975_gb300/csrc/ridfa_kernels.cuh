@@ -160,9 +160,38 @@ __device__ __forceinline__ uint32_t byte_of(uint32_t w, int q) { return (w >> (8
 // Table lookup policies.  A run's state is kept in the policy's own encoding (`enc`); `id`
 // recovers the automaton state number.
 //
-// Plain: compact uint16 table [(n+1) * C] and uint8 class map, in shared memory (or global
-// memory when it does not fit).  Lanes gathering different entries may hit the same bank.
+// Plain: the compact transition table in shared memory, entries premultiplied 16-bit byte
+// offsets (entry (s, c) at byte 2(s*C + c) holds 2*C*s'), so a step is one 3-input add and one
+// ld.shared.u16; the class table is the lane-replicated one of LutRep (conflict-free), holding 2c.
+// Lanes gathering different transition entries may share a bank.  Needs 2*C*(P+1) <= 64 KiB.
 struct LutPlain {
+    uint32_t lc, bt;          // this lane's class copy; the transition table
+    uint32_t row;             // 2*C: bytes per state row
+    static size_t smem_bytes(const Automaton &A) { return 256 * 128 + static_cast<size_t>(A.n + 1) * A.C * 2; }
+    static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n + 1) * A.C * 2 <= 0xFFFF; }
+    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+        row = 2 * A.C;
+        const uint32_t base_c = smem_addr(smem);
+        bt = base_c + 256 * 128;
+        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) sts_u32(base_c + i * 4, 2u * A.classmap[i >> 5]);
+        const uint32_t n = (A.n + 1) * A.C;
+        for (uint32_t i = threadIdx.x; i < (n + 1) / 2; i += blockDim.x) {
+            const uint32_t v0 = A.trans[2 * i] * row;
+            const uint32_t v1 = 2 * i + 1 < n ? A.trans[2 * i + 1] * row : 0u;
+            sts_u32(bt + i * 4, v0 | (v1 << 16));
+        }
+        lc = base_c + (threadIdx.x & 31) * 4;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id * row; }
+    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s / row; }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return lds_u16(bt + s + c); }
+};
+
+// Flat: the uint16 table [(n+1) * C] and uint8 class map through generic pointers, in shared
+// memory when the table fits there, else in global memory -- for automata too large for Plain.
+struct LutFlat {
     const uint16_t *t;
     const uint8_t *cls;
     uint32_t C;

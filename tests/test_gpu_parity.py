@@ -193,10 +193,10 @@ def test_text_paths_agree(path):
             assert np.array_equal(got[i], want[i])
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5])
 def test_tuning_variants_agree(mode):
-    """Every table layout (compact, lane-replicated 16/32-bit, half-replicated) and launch shape
-    gives the same bit-exact maps."""
+    """Every table layout (compact, lane-replicated 16/32-bit, half-replicated, generic loads) and
+    launch shape gives the same bit-exact maps."""
     x = textgen.c3_text(1 << 18, seed=77)
     for t in [dict(probe_interval=1), dict(probe_interval=64), dict(block_threads=64),
               dict(grid_blocks=1), dict(block_threads=128, grid_blocks=3),
@@ -212,8 +212,8 @@ def test_tuning_variants_agree(mode):
     z = textgen.c2_text(1 << 16, seed=79)
     # 424 states x 5 classes: the 16-bit offsets overflow and the 32-bit replicated table exceeds
     # shared memory; the compact table (automatic) and the half-replicated one (on request) fit
-    check(re2, z, 200, tuning=dict(table_mode=mode if mode in (1, 4) else 0), dfa_too=False)
-    check(re2, z, 1000, tuning=dict(table_mode=mode if mode in (1, 4) else 0, text_path=1), dfa_too=False)
+    check(re2, z, 200, tuning=dict(table_mode=mode if mode in (1, 4, 5) else 0), dfa_too=False)
+    check(re2, z, 1000, tuning=dict(table_mode=mode if mode in (1, 4, 5) else 0, text_path=1), dfa_too=False)
     prog = lib.ridfa_compile(re2)
     d = to_device(z)
     for bad in (2, 3):
