@@ -81,7 +81,14 @@ typedef struct {
 } ridfa_info;
 
 typedef struct {
-    uint32_t chunks_per_lane; /* reserved, must be 0 */
+    uint32_t piece_len;       /* intra-chunk speculation when the text has too few chunks to fill
+                                 the GPU: each chunk is cut into pieces of about this many bytes,
+                                 every piece is run from every state of the automaton, and the
+                                 piece functions are composed into the chunk's exact map row.
+                                 0 auto (on when fewer than 1/8 of the resident lanes would hold a
+                                 chunk, the automaton has at most RIDFA_MAX_SLOTS states and the
+                                 chunks are long enough; pieces of 256 bytes or more); 1 off;
+                                 >= 64 that piece length, when the other conditions hold */
     uint32_t block_threads;   /* threads per block of the reach kernel: 0 auto, a multiple of 32
                                  up to 1024 (512 when k > 128) */
     uint32_t probe_interval;  /* bytes between convergence checks of the speculative runs: 0 auto */

@@ -42,9 +42,9 @@ int cuda_fail(cudaError_t e) {
 int upload(const HostAutomaton &H, DeviceAutomaton &D, int dev) {
     D.device = dev;
     const size_t bt = H.trans.size() * 2, bf = H.final_bits.size() * 4, bi = H.ifmask.size() * 4,
-                 bs = H.slot_state.size() * 2;
+                 bs = H.slot_state.size() * 2, ba = static_cast<size_t>(H.n_states) * 2;
     auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
-    const size_t total = al(bt) + al(256) + al(bf) + al(bi) + al(bs);
+    const size_t total = al(bt) + al(256) + al(bf) + al(bi) + al(bs) + al(ba);
     uint8_t *base = nullptr;
     cudaError_t e = cudaMalloc(&base, total);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -54,12 +54,16 @@ int upload(const HostAutomaton &H, DeviceAutomaton &D, int dev) {
     D.final_bits = reinterpret_cast<uint32_t *>(base + off); off += al(bf);
     D.ifmask = reinterpret_cast<uint32_t *>(base + off); off += al(bi);
     D.slot_state = reinterpret_cast<uint16_t *>(base + off); off += al(bs);
+    D.all_states = reinterpret_cast<uint16_t *>(base + off); off += al(ba);
     D.bytes = total;
+    std::vector<uint16_t> iota(H.n_states);
+    for (uint32_t i = 0; i < H.n_states; ++i) iota[i] = static_cast<uint16_t>(i);
     e = cudaMemcpy(D.trans, H.trans.data(), bt, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(D.classmap, H.classmap.data(), 256, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && bf) e = cudaMemcpy(D.final_bits, H.final_bits.data(), bf, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && bi) e = cudaMemcpy(D.ifmask, H.ifmask.data(), bi, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && bs) e = cudaMemcpy(D.slot_state, H.slot_state.data(), bs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ba) e = cudaMemcpy(D.all_states, iota.data(), ba, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(base);
         D = DeviceAutomaton{};
@@ -878,12 +882,78 @@ __global__ void __launch_bounds__(kJoinThreads) rid_join_kernel(JoinArgs p) {
     *p.accept = acc;
 }
 
+// ------------------------------------------------------------ intra-chunk speculation (pieces)
+// A chunk cut into pieces y_i = p_1 ... p_s: each piece is run from every state x of the automaton
+// (the reach kernel with every state as a slot), giving f_j(x) = δ(x, p_j) or ⊥, and
+// δ(x, y_i) = f_s(...f_1(x)) because the automaton is deterministic; the chunk's map row is that
+// composition applied to the interface slots' start states.  Exact, whatever the convergence.
+constexpr uint32_t kComposeGroup = 32;     // functions composed per thread and level
+
+// One level: function g of chunk i = the composition, in order, of input functions
+// [g*G, (g+1)*G) of that chunk.  One thread per (chunk, group, start state).
+__global__ void rid_compose_kernel(const uint16_t *in, uint32_t in_per_chunk, uint16_t *out, uint32_t out_per_chunk,
+                                   uint32_t c, uint32_t P) {
+    const uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= static_cast<uint64_t>(c) * out_per_chunk * P) return;
+    const uint32_t x = static_cast<uint32_t>(t % P);
+    const uint64_t cg = t / P;
+    const uint64_t g = cg % out_per_chunk, i = cg / out_per_chunk;
+    const uint64_t f0 = i * in_per_chunk + g * kComposeGroup;
+    const uint64_t f1 = min(f0 + kComposeGroup, (i + 1) * in_per_chunk);
+    uint32_t y = x;
+    for (uint64_t f = f0; f < f1 && y != kUndef; ++f) y = in[f * P + y];
+    out[cg * P + x] = static_cast<uint16_t>(y);
+}
+
+// Chunk map rows from the composed functions F_i: λ_i(a) = F_i(start state of slot a), and each
+// row's D_i summary (number of distinct defined end states and the smallest).  One warp per chunk.
+__global__ void rid_apply_kernel(const uint16_t *F, uint32_t P, const uint16_t *slot_state, uint32_t k, uint32_t c,
+                                 uint16_t *maps, uint32_t *dinfo, uint32_t *status, const uint32_t *piece_status) {
+    const uint64_t i = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    if (i == 0 && lane == 0) {
+        // failures of the pieces' reach carry over; their "wide" bit does not (pieces are not joined)
+        const uint32_t ps = *piece_status & (kStatusBad | kStatusTimeout);
+        if (ps) atomicOr(status, ps);
+    }
+    if (i >= c) return;                       // whole warps leave together
+    constexpr int kMaxR = RIDFA_MAX_SLOTS / 32;
+    uint32_t v[kMaxR];
+#pragma unroll
+    for (int r = 0; r < kMaxR; ++r) {
+        const uint32_t a = r * 32 + lane;
+        v[r] = a < k ? F[i * P + slot_state[a]] : kUndef;
+        if (a < k) maps[i * k + a] = static_cast<uint16_t>(v[r]);
+    }
+    uint32_t cnt = 0, first = kUndef, cur = 0;
+    for (;;) {
+        uint32_t m = 0xFFFFFFFFu;
+#pragma unroll
+        for (int r = 0; r < kMaxR; ++r)
+            if (v[r] != kUndef && (cnt == 0 || v[r] > cur)) m = min(m, v[r]);
+        m = __reduce_min_sync(kFull, m);
+        if (m == 0xFFFFFFFFu) break;
+        if (cnt == 0) first = m;
+        cur = m;
+        if (++cnt > kMaxD) break;
+    }
+    if (lane == 0) {
+        if (cnt > kMaxD) {
+            dinfo[i] = (0xFFu << 16) | first;
+            atomicOr(status, kStatusWide);
+        } else {
+            dinfo[i] = cnt ? ((cnt << 16) | first) : static_cast<uint32_t>(kUndef);
+        }
+    }
+}
+
 struct Layout {   // scratch layout for one call
     size_t maps_off, dinfo_off, partials_off, ticket_off, status_off, accept_off, runs_off, finals_off,
-        summary_off, total;
+        summary_off, pmaps_off, pdinfo_off, comp_off, total;
 };
 
-Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks, uint64_t grid_warps) {
+Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks, uint64_t grid_warps,
+                  uint64_t pieces = 0, uint32_t P = 0, uint64_t comp_funcs = 0) {
     auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
     Layout L{};
     size_t off = 0;
@@ -895,6 +965,9 @@ Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks, 
     L.runs_off = off; off += al(grid_warps * kRunsPerWarp * sizeof(RunEntry));
     L.finals_off = off; off += al(grid_warps * kFinalsPerWarp * 4);
     L.summary_off = off; off += al(sizeof(ridfa_shard_summary));
+    L.pmaps_off = off; off += al(pieces * P * 2);
+    L.pdinfo_off = off; off += al(pieces * 4);
+    L.comp_off = off; off += 2 * al(comp_funcs * P * 2);      // two buffers of composed functions
     L.maps_off = off; off += need_maps ? al(c * k * 2) : 0;
     L.total = off;
     return L;
@@ -1120,16 +1193,35 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
                (static_cast<uint64_t>(kJoinThreads) * per_thread)));
     Automaton A{D->trans, D->classmap, D->final_bits, D->ifmask, D->slot_state,
                 H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+    // intra-chunk speculation: too few chunks to fill the GPU, each long enough to cut into pieces
+    const uint32_t piece_req = tuning ? tuning->piece_len : 0;
+    if (piece_req > 1 && piece_req < 64) return RIDFA_E_ARG;
+    uint64_t spc = 1;                                  // pieces per chunk
+    if (piece_req != 1 && H.n_states >= 1 && H.n_states <= RIDFA_MAX_SLOTS) {
+        const uint64_t lanes = static_cast<uint64_t>(sms) * 1024;
+        if (c * 8 < lanes) {
+            const uint64_t plen = piece_req >= 64 ? piece_req : 256;
+            spc = std::min<uint64_t>(2 * lanes / c, len / (c * plen));
+            if (spc < 2) spc = 1;
+        }
+    }
+    const uint64_t pieces = c * spc;
+    const uint32_t NS = H.n_states;
+    Automaton Aall{D->trans, D->classmap, D->final_bits, D->ifmask, D->all_states,
+                   H.n_states, H.n_classes, NS, (NS + 31) / 32, 0};
     // plan the reach launch first: the run-list scratch is sized by its grid
-    ReachArgs ra{A, d_text, len, n_chunks, nullptr, nullptr, nullptr, 8, nullptr, nullptr};
+    ReachArgs ra{spc > 1 ? Aall : A, d_text, len, static_cast<uint32_t>(pieces), nullptr, nullptr, nullptr, 8,
+                 nullptr, nullptr};
     if (tuning && tuning->probe_interval) ra.probe = tuning->probe_interval;
     ReachPlan plan;
-    err = plan_reach(A, tuning, d_text, ra, sms, &plan);
+    err = plan_reach(ra.A, tuning, d_text, ra, sms, &plan);
     if (err != RIDFA_OK) return err;
     // warps past the last 32-chunk task never write their run list
     const uint64_t grid_warps = std::min<uint64_t>(static_cast<uint64_t>(plan.grid) * (plan.block / 32),
-                                                   (n_chunks + 31) / 32);
-    const Layout L = layout_for(c, H.k, d_maps_user == nullptr, join_blocks, grid_warps);
+                                                   (pieces + 31) / 32);
+    const uint64_t comp_funcs = spc > 1 ? c * ((spc + kComposeGroup - 1) / kComposeGroup) : 0;
+    const Layout L = layout_for(c, H.k, d_maps_user == nullptr, join_blocks, grid_warps, spc > 1 ? pieces : 0,
+                                spc > 1 ? NS : 0, comp_funcs);
     DeviceScratch *S = scratch_for(P, dev, L.total, &err);
     if (!S) return err;
     uint8_t *base = static_cast<uint8_t *>(S->base);
@@ -1139,12 +1231,13 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     uint16_t *maps = d_maps_user ? d_maps_user : reinterpret_cast<uint16_t *>(base + L.maps_off);
     uint32_t *dinfo = reinterpret_cast<uint32_t *>(base + L.dinfo_off);
     uint32_t *partials = reinterpret_cast<uint32_t *>(base + L.partials_off);
-    ra.maps = maps;
-    ra.dinfo = dinfo;
-    ra.status = status;
+    uint32_t *piece_status = status + 1;
+    ra.maps = spc > 1 ? reinterpret_cast<uint16_t *>(base + L.pmaps_off) : maps;
+    ra.dinfo = spc > 1 ? reinterpret_cast<uint32_t *>(base + L.pdinfo_off) : dinfo;
+    ra.status = spc > 1 ? piece_status : status;
     ra.runs = reinterpret_cast<RunEntry *>(base + L.runs_off);
     ra.finals = reinterpret_cast<uint32_t *>(base + L.finals_off);
-    e = cudaMemsetAsync(status, 0, 4, st);
+    e = cudaMemsetAsync(status, 0, 8, st);
     if (e != cudaSuccess) return cuda_fail(e);
 
     const bool prof = tuning && tuning->profile;
@@ -1160,6 +1253,28 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     }
     e = reach_dispatch(ra, plan, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
+    if (spc > 1) {
+        // compose each chunk's piece functions, kComposeGroup per thread and level, then apply
+        // them to the interface slots' start states
+        const uint16_t *in = ra.maps;
+        uint64_t in_per = spc;
+        uint16_t *bufs[2] = {reinterpret_cast<uint16_t *>(base + L.comp_off),
+                             reinterpret_cast<uint16_t *>(base + L.comp_off + ((comp_funcs * NS * 2 + 255) & ~255ull))};
+        int b = 0;
+        while (in_per > 1) {
+            const uint64_t out_per = (in_per + kComposeGroup - 1) / kComposeGroup;
+            const uint64_t threads = c * out_per * NS;
+            rid_compose_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(
+                in, static_cast<uint32_t>(in_per), bufs[b], static_cast<uint32_t>(out_per), static_cast<uint32_t>(c), NS);
+            in = bufs[b];
+            b ^= 1;
+            in_per = out_per;
+        }
+        rid_apply_kernel<<<static_cast<unsigned>((c * 32 + 255) / 256), 256, 0, st>>>(
+            in, NS, D->slot_state, H.k, static_cast<uint32_t>(c), maps, dinfo, status, piece_status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     if (prof) cudaEventRecord(static_cast<cudaEvent_t>(S->ev[1]), st);
 
     // ---- join

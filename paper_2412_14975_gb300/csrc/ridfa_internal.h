@@ -37,6 +37,7 @@ struct DeviceAutomaton {
     uint32_t *final_bits = nullptr;
     uint32_t *ifmask = nullptr;
     uint16_t *slot_state = nullptr;
+    uint16_t *all_states = nullptr;   // [n_states]: state s (every state as a start, for pieces)
     size_t bytes = 0;
 };
 

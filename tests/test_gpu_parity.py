@@ -153,6 +153,45 @@ def test_many_distinct_end_states(nb):
     check(re_src, y, 100, dfa_too=False)
 
 
+def test_piece_speculation_maps():
+    """Few long chunks: each chunk is cut into pieces run from every automaton state and the piece
+    functions are composed into the chunk's row.  Pieces forced on at several lengths, and off,
+    give the oracle's maps; also for the all-states DFA comparator and for rows with more than 32
+    distinct end states (composed rows, then the sequential join)."""
+    x3 = textgen.c3_text(400_000, seed=95)
+    x1 = textgen.c1_text(300_000, seed=96)
+    for re_src, x in [(textgen.C3_RE, x3), (textgen.C1_RE, x1), (textgen.regexp_family_re(3),
+                                                                  textgen.regexp_family_text(200_000, 97))]:
+        o, ser = oracle(re_src)
+        prog = lib.ridfa_compile(re_src)
+        d = to_device(x)
+        want_acc = ser.accepts(x)
+        for c in (1, 3, 64):
+            want = o.lambda_rows(x, c)
+            dwant = o.dfa_lambda_rows(x, c)
+            for piece in (0, 1, 64, 1000):
+                acc, maps = run(lib, prog, d, x.size, c, tuning=dict(piece_len=piece))
+                assert acc == want_acc
+                for i in range(c):
+                    assert np.array_equal(maps[i], want[i]), (re_src[:20], c, piece, i)
+                dacc, dmaps = run(lib, prog, d, x.size, c, dfa=True, tuning=dict(piece_len=piece))
+                assert dacc == want_acc
+                for i in range(c):
+                    assert np.array_equal(dmaps[i], dwant[i]), (re_src[:20], c, piece, i)
+    y, _ = textgen.mutate(x3, seed=98, n_subs=3)
+    check(textgen.C3_RE, y, 5, tuning=dict(piece_len=64))
+    re_src, xs, ys = _branches_re(40)
+    rng = np.random.Generator(np.random.PCG64(99))
+    parts = [xs[int(i)] + "a" * int(rng.integers(0, 300)) + ys[int(i)] for i in rng.integers(40, size=200)]
+    z = np.frombuffer("".join(parts).encode(), dtype=np.uint8)
+    for c in (2, 9):
+        check(re_src, z, c, tuning=dict(piece_len=64), dfa_too=False)
+    prog = lib.ridfa_compile(textgen.C1_RE)
+    with pytest.raises(lib.RidfaError) as e:
+        lib.ridfa_recognize(prog, to_device(x1), x1.size, 4, tuning=dict(piece_len=17))
+    assert e.value.code == -1
+
+
 def test_multi_run_handoff_rows():
     """Chunks whose live runs never merge into one state (the {2,4} codon RE keeps up to five
     distinct states) are handed off as several runs each; with ~1 KiB chunks a warp holds over 32
