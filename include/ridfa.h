@@ -83,8 +83,9 @@ typedef struct {
 typedef struct {
     uint32_t piece_len;       /* intra-chunk speculation when the text has too few chunks to fill
                                  the GPU: each chunk is cut into pieces of about this many bytes,
-                                 every piece is run from every state of the automaton, and the
-                                 piece functions are composed into the chunk's exact map row.
+                                 every piece is run (one warp, lockstep) from every state of the
+                                 automaton, and the piece functions are composed into the chunk's
+                                 exact map row.
                                  0 auto (on when fewer than 1/8 of the resident lanes would hold a
                                  chunk, the automaton has at most RIDFA_MAX_SLOTS states and the
                                  chunks are long enough; pieces of 256 bytes or more); 1 off;

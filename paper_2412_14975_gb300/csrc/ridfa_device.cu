@@ -883,6 +883,85 @@ __global__ void __launch_bounds__(kJoinThreads) rid_join_kernel(JoinArgs p) {
 }
 
 // ------------------------------------------------------------ intra-chunk speculation (pieces)
+// One warp per piece, the whole piece in lockstep: lanes hold the runs from every state (state
+// a = 32*r + lane in register r), every lane reads the same 16 bytes (one transaction), the
+// class lookup is the lane's own replica, and registers whose runs all died are skipped.  The
+// piece's row (f_j(x) for every state x, kUndef when the run dies) is written at the end.
+template <int R, class LUT>
+__global__ void __launch_bounds__(256) rid_piece_kernel(ReachArgs p, int table_in_smem) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const Automaton &A = p.A;
+    LUT T;
+    T.setup(A, smem, table_in_smem != 0);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t dead = T.enc(A.n);
+    const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t j = warp0; j < p.c; j += n_warps) {
+        uint32_t s[R];
+        uint32_t live = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t a = r * 32 + lane;
+            s[r] = a < A.k ? T.enc(__ldg(A.slot_state + a)) : dead;
+            if (r * 32 < static_cast<int>(A.k)) live |= 1u << r;
+        }
+        uint64_t pos = chunk_begin(j, p.len, p.c);
+        const uint64_t end = chunk_begin(j + 1, p.len, p.c);
+        auto step = [&](uint32_t b) {
+            const uint32_t c = T.cls_of(b);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (live & (1u << r)) s[r] = T.next(s[r], c);
+        };
+        while (pos < end && (reinterpret_cast<uintptr_t>(p.text + pos) & 15)) step(__ldg(p.text + pos++));
+        while (pos + 16 <= end && live) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.text + pos));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const uint32_t c = T.cls_at(w[q >> 2], q & 3);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (live & (1u << r)) s[r] = T.next(s[r], c);
+            }
+            pos += 16;
+            uint32_t nl = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (__any_sync(kFull, s[r] != dead)) nl |= 1u << r;
+            live &= nl;
+        }
+        while (pos < end && live) step(__ldg(p.text + pos++));
+        uint16_t *row = p.maps + j * A.k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t a = r * 32 + lane;
+            if (a < A.k) row[a] = s[r] == dead ? kUndef : static_cast<uint16_t>(T.id(s[r]));
+        }
+    }
+}
+
+template <int R, class LUT>
+cudaError_t piece_one(const ReachArgs &a, int grid, size_t smem, int tis, cudaStream_t st) {
+    auto kern = rid_piece_kernel<R, LUT>;
+    cudaError_t e = ensure_smem_cap(reinterpret_cast<const void *>(kern), smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, smem, st>>>(a, tis);
+    return cudaGetLastError();
+}
+
+template <class LUT>
+cudaError_t piece_r(int R, const ReachArgs &a, int grid, size_t smem, int tis, cudaStream_t st) {
+    switch (R) {
+        case 1: return piece_one<1, LUT>(a, grid, smem, tis, st);
+        case 2: return piece_one<2, LUT>(a, grid, smem, tis, st);
+        case 4: return piece_one<4, LUT>(a, grid, smem, tis, st);
+        default: return piece_one<8, LUT>(a, grid, smem, tis, st);
+    }
+}
+
 // A chunk cut into pieces y_i = p_1 ... p_s: each piece is run from every state x of the automaton
 // (the reach kernel with every state as a slot), giving f_j(x) = δ(x, p_j) or ⊥, and
 // δ(x, y_i) = f_s(...f_1(x)) because the automaton is deterministic; the chunk's map row is that
@@ -1065,6 +1144,20 @@ cudaError_t reach_dispatch(const ReachArgs &a, const ReachPlan &pl, cudaStream_t
     }
 }
 
+// Launch the piece kernel with the table layout a reach plan chose (table only, no staging).
+cudaError_t piece_dispatch(const ReachArgs &a, const ReachPlan &pl, int sms, cudaStream_t st) {
+    const size_t smem = pl.path == kPathGlobal ? pl.smem : pl.staging_offset;
+    const uint64_t blocks = (static_cast<uint64_t>(a.c) + 7) / 8;
+    const int grid = static_cast<int>(std::min<uint64_t>(blocks, static_cast<uint64_t>(sms) * 8));
+    switch (pl.mode) {
+        case kModeRep16: return piece_r<LutRep<true>>(pl.R, a, grid, smem, pl.tis, st);
+        case kModeRep32: return piece_r<LutRep<false>>(pl.R, a, grid, smem, pl.tis, st);
+        case kModePart16: return piece_r<LutPart>(pl.R, a, grid, smem, pl.tis, st);
+        case kModePlain: return piece_r<LutPlain>(pl.R, a, grid, smem, pl.tis, st);
+        default: return piece_r<LutFlat>(pl.R, a, grid, smem, pl.tis, st);
+    }
+}
+
 // Choose the layout of a reach launch.  Defaults: the smallest lane-replicated table that fits
 // (16-bit, then 32-bit offsets), else the compact table; text staged by bulk copies when the
 // text is 16-byte aligned and the staging ring fits next to the table; one block per SM with
@@ -1216,9 +1309,9 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     ReachPlan plan;
     err = plan_reach(ra.A, tuning, d_text, ra, sms, &plan);
     if (err != RIDFA_OK) return err;
-    // warps past the last 32-chunk task never write their run list
-    const uint64_t grid_warps = std::min<uint64_t>(static_cast<uint64_t>(plan.grid) * (plan.block / 32),
-                                                   (pieces + 31) / 32);
+    // warps past the last 32-chunk task never write their run list (the piece kernel has none)
+    const uint64_t grid_warps = spc > 1 ? 0 : std::min<uint64_t>(static_cast<uint64_t>(plan.grid) * (plan.block / 32),
+                                                                 (pieces + 31) / 32);
     const uint64_t comp_funcs = spc > 1 ? c * ((spc + kComposeGroup - 1) / kComposeGroup) : 0;
     const Layout L = layout_for(c, H.k, d_maps_user == nullptr, join_blocks, grid_warps, spc > 1 ? pieces : 0,
                                 spc > 1 ? NS : 0, comp_funcs);
@@ -1251,7 +1344,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
             }
         cudaEventRecord(static_cast<cudaEvent_t>(S->ev[0]), st);
     }
-    e = reach_dispatch(ra, plan, st, nullptr);
+    e = spc > 1 ? piece_dispatch(ra, plan, sms, st) : reach_dispatch(ra, plan, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
     if (spc > 1) {
         // compose each chunk's piece functions, kComposeGroup per thread and level, then apply
