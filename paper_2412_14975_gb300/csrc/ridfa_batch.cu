@@ -441,6 +441,7 @@ struct LaunchGroup {          // one persistent reach launch
     std::vector<uint32_t> progs;   // batch program indices in this launch
     uint32_t task0 = 0, n_tasks = 0;
     size_t table_smem = 0;
+    uint64_t run0 = 0;             // first warp of this launch's run lists (groups may run at once)
     int block = 0, grid = 0;
     uint32_t stg = 0;              // staging offset in dynamic shared memory
     size_t smem = 0;               // dynamic shared memory
@@ -647,7 +648,8 @@ int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, co
         if (err != RIDFA_OK) return err;
         if (per_sm < 1) return RIDFA_E_UNSUPPORTED;
         g.grid = static_cast<int>(std::min<uint64_t>(g.n_tasks, static_cast<uint64_t>(sms) * per_sm));
-        run_warps = std::max<uint64_t>(run_warps, static_cast<uint64_t>(g.grid) * warps);
+        g.run0 = run_warps;
+        run_warps += static_cast<uint64_t>(g.grid) * warps;
         P.groups.push_back(g);
     }
     // join segments
@@ -714,7 +716,30 @@ void plan_image(const BatchPlan *pl, uint8_t *base, uint8_t *img) {
     if (!P.segs.empty()) std::memcpy(img + P.o_segs, P.segs.data(), P.segs.size() * sizeof(SegDesc));
 }
 
-int plan_enqueue(const BatchPlan *pl, uint8_t *base, uint8_t *d_accept, cudaStream_t st, bool zero_counters) {
+int make_fork(LaunchFork *f) {
+    f->ok = false;
+    for (int i = 0; i < kMaxLaunchGroups - 1; ++i) {
+        cudaError_t e = cudaStreamCreateWithFlags(&f->aux[i], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    for (int i = 0; i < kMaxLaunchGroups; ++i) {
+        cudaError_t e = cudaEventCreateWithFlags(&f->ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    f->ok = true;
+    return RIDFA_OK;
+}
+
+void free_fork(LaunchFork *f) {
+    for (auto &s : f->aux)
+        if (s) cudaStreamDestroy(s);
+    for (auto &e : f->ev)
+        if (e) cudaEventDestroy(e);
+    *f = LaunchFork{};
+}
+
+int plan_enqueue(const BatchPlan *pl, uint8_t *base, uint8_t *d_accept, cudaStream_t st, bool zero_counters,
+                 const LaunchFork *fork) {
     const BatchPlan &P = *pl;
     uint32_t *counters = reinterpret_cast<uint32_t *>(base + P.o_counters);
     uint32_t *status = counters + 32;
@@ -726,12 +751,26 @@ int plan_enqueue(const BatchPlan *pl, uint8_t *base, uint8_t *d_accept, cudaStre
     const TaskDesc *tasks = reinterpret_cast<const TaskDesc *>(base + P.o_tasks);
     RunEntry *runs = reinterpret_cast<RunEntry *>(base + P.o_runs);
     uint32_t *finals = reinterpret_cast<uint32_t *>(base + P.o_finals);
+    const bool concurrent = fork && fork->ok && P.groups.size() > 1 && P.groups.size() <= kMaxLaunchGroups;
+    if (concurrent) {
+        cudaError_t e = cudaEventRecord(fork->ev[0], st);
+        for (size_t gi = 1; gi < P.groups.size() && e == cudaSuccess; ++gi) e = cudaStreamWaitEvent(fork->aux[gi - 1], fork->ev[0], 0);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     for (size_t gi = 0; gi < P.groups.size(); ++gi) {
         const LaunchGroup &g = P.groups[gi];
         if (g.n_tasks == 0) continue;
-        BatchReachArgs a{progs, tasks + g.task0, g.n_tasks, 8, counters + gi, status, runs, finals};
-        cudaError_t e = batch_reach(g, a, st, nullptr);
+        BatchReachArgs a{progs, tasks + g.task0, g.n_tasks, 8, counters + gi, status, runs + g.run0 * kRunsPerWarp,
+                         finals + g.run0 * kFinalsPerWarp};
+        cudaError_t e = batch_reach(g, a, (concurrent && gi > 0) ? fork->aux[gi - 1] : st, nullptr);
         if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (concurrent) {
+        for (size_t gi = 1; gi < P.groups.size(); ++gi) {
+            cudaError_t e = cudaEventRecord(fork->ev[gi], fork->aux[gi - 1]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, fork->ev[gi], 0);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
     }
     if (!P.segs.empty()) {
         BatchJoinArgs J{progs, reinterpret_cast<const TextDesc *>(base + P.o_texts),
@@ -759,6 +798,7 @@ struct ridfa_batch {
     size_t dbytes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    ridfa::LaunchFork fork;
 };
 
 namespace ridfa {
@@ -799,7 +839,7 @@ int batch_build(ridfa_batch *B, uint32_t L) {
         e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e);
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        err = e == cudaSuccess ? plan_enqueue(B->plan, base, B->d_accept, cs, true) : cuda_fail(e);
+        err = e == cudaSuccess ? plan_enqueue(B->plan, base, B->d_accept, cs, true, &B->fork) : cuda_fail(e);
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
@@ -820,7 +860,7 @@ int batch_run(ridfa_batch *B, cudaStream_t st) {
         cudaError_t e = cudaGraphLaunch(B->exec, st);
         return e == cudaSuccess ? RIDFA_OK : cuda_fail(e);
     }
-    return plan_enqueue(B->plan, static_cast<uint8_t *>(B->dmem), B->d_accept, st, true);
+    return plan_enqueue(B->plan, static_cast<uint8_t *>(B->dmem), B->d_accept, st, true, &B->fork);
 }
 
 // Chunk length for the batch.  Every program is keyed by (log2 |P|, log2 k, log2 C); when all
@@ -915,12 +955,13 @@ extern "C" int ridfa_batch_create(const ridfa_program *const *progs, uint32_t n_
     B->d_accept = d_accept;
     B->use_graph = !(opts && opts->no_graph);
     uint32_t L = opts ? opts->chunk_len : 0;
-    int err = RIDFA_OK;
-    if (L == 0) err = ridfa::batch_autotune(B, &L);
+    int err = ridfa::make_fork(&B->fork);
+    if (err == RIDFA_OK && L == 0) err = ridfa::batch_autotune(B, &L);
     if (err == RIDFA_OK) err = ridfa::batch_build(B, L);
     if (err != RIDFA_OK) {
         ridfa::batch_release(B);
         ridfa::plan_delete(B->plan);
+        ridfa::free_fork(&B->fork);
         delete B;
         return err;
     }
@@ -958,6 +999,7 @@ extern "C" void ridfa_batch_free(ridfa_batch *b) {
     cudaDeviceSynchronize();
     ridfa::batch_release(b);
     ridfa::plan_delete(b->plan);
+    ridfa::free_fork(&b->fork);
     cudaSetDevice(cur);
     (void)cudaGetLastError();
     delete b;

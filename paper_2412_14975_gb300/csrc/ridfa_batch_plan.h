@@ -36,9 +36,23 @@ size_t plan_status_offset(const BatchPlan *pl);  // byte offset of the status wo
 // descriptors depend on it); `img` holds plan_image_bytes bytes.
 void plan_image(const BatchPlan *pl, uint8_t *base, uint8_t *img);
 
+// Streams and events that let the reach groups of one batch (one per table layout) run
+// concurrently: group 0 on the caller's stream, group g > 0 on aux[g - 1], joined back before the
+// join launch.  Owned by the caller; created once with make_fork, released with free_fork.
+constexpr int kMaxLaunchGroups = 4;
+struct LaunchFork {
+    cudaStream_t aux[kMaxLaunchGroups - 1] = {};
+    cudaEvent_t ev[kMaxLaunchGroups] = {};
+    bool ok = false;
+};
+int make_fork(LaunchFork *f);
+void free_fork(LaunchFork *f);
+
 // Enqueue the reach groups and the join on `st` for a block at `base` whose image is in place.
-// zero_counters: clear the task tickets and status word first (graph replays).
-int plan_enqueue(const BatchPlan *pl, uint8_t *base, uint8_t *d_accept, cudaStream_t st, bool zero_counters);
+// zero_counters: clear the task tickets and status word first (graph replays).  fork: run the
+// reach groups concurrently (null: one after another on `st`).
+int plan_enqueue(const BatchPlan *pl, uint8_t *base, uint8_t *d_accept, cudaStream_t st, bool zero_counters,
+                 const LaunchFork *fork = nullptr);
 
 struct PlanStats {
     uint64_t total_bytes, total_chunks;

@@ -122,6 +122,7 @@ struct Slot {                          // one launch slot: a batch in flight at 
     size_t hcap = 0;
     uint8_t *dacc = nullptr;           // device accept bytes [max_batch_requests]
     uint8_t *hacc = nullptr;           // pinned: accept bytes, then the status word
+    LaunchFork fork;                   // the batch's reach groups run concurrently
     std::vector<Request> reqs;
     bool busy = false;
 };
@@ -269,7 +270,7 @@ void launch(ridfa_server *S, Slot &sl, std::vector<Request> &batch) {
         cudaError_t e = cudaMemcpyAsync(sl.dblock, sl.himg, img, cudaMemcpyHostToDevice, sl.st);
         if (e != cudaSuccess) err = cuda_fail(e);
     }
-    if (err == RIDFA_OK) err = plan_enqueue(sl.plan, sl.dblock, sl.dacc, sl.st, false);
+    if (err == RIDFA_OK) err = plan_enqueue(sl.plan, sl.dblock, sl.dacc, sl.st, false, &sl.fork);
     if (err == RIDFA_OK) {
         const size_t so = (static_cast<size_t>(S->o.max_batch_requests) + 15) & ~static_cast<size_t>(15);
         cudaError_t e = cudaMemcpyAsync(sl.hacc, sl.dacc, n, cudaMemcpyDeviceToHost, sl.st);
@@ -370,6 +371,7 @@ void release_server(ridfa_server *S) {
         if (sl.himg) cudaFreeHost(sl.himg);
         if (sl.dacc) cudaFree(sl.dacc);
         if (sl.hacc) cudaFreeHost(sl.hacc);
+        free_fork(&sl.fork);
         plan_delete(sl.plan);
     }
     S->slots.clear();
@@ -425,6 +427,7 @@ extern "C" int ridfa_server_create(const ridfa_server_opts *opts, ridfa_server *
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&sl.dacc), o.max_batch_requests);
         if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&sl.hacc), so + 16, cudaHostAllocDefault);
         if (e != cudaSuccess) err = ridfa::cuda_fail(e);
+        if (err == RIDFA_OK) err = ridfa::make_fork(&sl.fork);
     }
     if (err != RIDFA_OK) {
         ridfa::release_server(S);
