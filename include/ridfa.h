@@ -86,9 +86,10 @@ typedef struct {
                                  every piece is run (one warp, lockstep) from every state of the
                                  automaton, and the piece functions are composed into the chunk's
                                  exact map row.
-                                 0 auto (on when fewer than 1/8 of the resident lanes would hold a
-                                 chunk, the automaton has at most RIDFA_MAX_SLOTS states and the
-                                 chunks are long enough; pieces of 256 bytes or more); 1 off;
+                                 0 auto (on when the chunks would keep few of the resident warps
+                                 busy -- fewer than warps / (4 * (1 + ceil(P/32))) chunks -- the
+                                 automaton has at most RIDFA_MAX_SLOTS states and the chunks are
+                                 long enough; pieces of 256 bytes or more); 1 off;
                                  >= 64 that piece length, when the other conditions hold */
     uint32_t block_threads;   /* threads per block of the reach kernel: 0 auto, a multiple of 32
                                  up to 1024 (512 when k > 128) */
@@ -100,8 +101,10 @@ typedef struct {
                                  16-bit offsets in shared memory, else the uint16 table through
                                  generic loads); 2 lane-replicated 16-bit offsets; 3
                                  lane-replicated 32-bit offsets; 4 half-replicated (16 copies of
-                                 the transition table); 5 the uint16 table through generic loads
-                                 (E_ARG if the chosen layout does not fit) */
+                                 the transition table); 5 the uint16 table through generic loads;
+                                 6 lane-replicated 16-bit entries in 4-byte units (tables up to
+                                 4x larger than mode 2 allows) (E_ARG if the chosen layout does not
+                                 fit) */
     uint32_t text_path;       /* how the converged runs read the text: 0 auto; 1 each lane's own
                                  16-byte global loads; 2 per-lane bulk copies (cp.async.bulk)
                                  into a shared-memory ring; 3 warp-cooperative coalesced loads

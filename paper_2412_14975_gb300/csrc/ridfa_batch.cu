@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kBatchJoinThreads) rid_join_batch_kernel(Batch
 }
 
 // ---------------------------------------------------------------------------- host side
-enum BMode : uint32_t { kBPlain = 1, kBRep16 = 2, kBRep32 = 3, kBFlat = 4 };
+enum BMode : uint32_t { kBPlain = 1, kBRep16 = 2, kBRep32 = 3, kBFlat = 4, kBRep16x4 = 5 };
 
 struct LaunchGroup {          // one persistent reach launch
     uint32_t mode = kBPlain;
@@ -475,6 +475,7 @@ cudaError_t batch_reach(const LaunchGroup &g, const BatchReachArgs &a, cudaStrea
             case kBRep16: return batch_reach_r<LutRep<true>, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
             case kBRep32: return batch_reach_r<LutRep<false>, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
             case kBPlain: return batch_reach_r<LutPlain, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+            case kBRep16x4: return batch_reach_r<LutRep16x4, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
             default: return batch_reach_r<LutFlat, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
         }
     }
@@ -482,6 +483,7 @@ cudaError_t batch_reach(const LaunchGroup &g, const BatchReachArgs &a, cudaStrea
         case kBRep16: return batch_reach_r<LutRep<true>, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
         case kBRep32: return batch_reach_r<LutRep<false>, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
         case kBPlain: return batch_reach_r<LutPlain, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
+        case kBRep16x4: return batch_reach_r<LutRep16x4, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
         default: return batch_reach_r<LutFlat, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
     }
 }
@@ -584,6 +586,12 @@ int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, co
                      pln = LutPlain::smem_bytes(A), flt = LutFlat::smem_bytes(A);
         if (LutRep<true>::fits16(A) && r16 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep16; tbytes[p] = r16; }
         else if (r32 + 8 * kWarpCoopBytes <= limit) { mode[p] = kBRep32; tbytes[p] = r32; }
+        // (the scaled 16-bit table only when 16 warps' staging still fits beside it: its launch
+        // group takes the warp count of its largest table)
+        else if (LutRep16x4::fits(A) && LutRep16x4::smem_bytes(A) + 16 * kWarpCoopBytes <= limit) {
+            mode[p] = kBRep16x4;
+            tbytes[p] = LutRep16x4::smem_bytes(A);
+        }
         else if (LutPlain::fits(A) && pln + 8 * kWarpCoopBytes <= limit) { mode[p] = kBPlain; tbytes[p] = pln; }
         else if (flt + 8 * kWarpCoopBytes <= limit) { mode[p] = kBFlat; P.tis[p] = 1; tbytes[p] = flt; }
         else { mode[p] = kBFlat; P.tis[p] = 0; tbytes[p] = 256; }
@@ -618,7 +626,7 @@ int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, co
     P.groups.clear();
     P.tasks.clear();
     uint64_t run_warps = 0;
-    for (uint32_t m = kBPlain; m <= kBFlat; ++m) {
+    for (uint32_t m = kBPlain; m <= kBRep16x4; ++m) {
         LaunchGroup g;
         g.mode = m;
         g.coop = aligned_all;

@@ -39,7 +39,7 @@ void plan_image(const BatchPlan *pl, uint8_t *base, uint8_t *img);
 // Streams and events that let the reach groups of one batch (one per table layout) run
 // concurrently: group 0 on the caller's stream, group g > 0 on aux[g - 1], joined back before the
 // join launch.  Owned by the caller; created once with make_fork, released with free_fork.
-constexpr int kMaxLaunchGroups = 4;
+constexpr int kMaxLaunchGroups = 5;
 struct LaunchFork {
     cudaStream_t aux[kMaxLaunchGroups - 1] = {};
     cudaEvent_t ev[kMaxLaunchGroups] = {};

@@ -1081,7 +1081,8 @@ DeviceScratch *scratch_for(const ridfa_program *P, int dev, size_t bytes, int *e
     return S;
 }
 
-enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3, kModePart16 = 4, kModeFlat = 5 };
+enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3, kModePart16 = 4, kModeFlat = 5,
+                       kModeRep16x4 = 6 };
 
 // How one reach launch is laid out: table layout, text path, block/grid, shared memory.
 struct ReachPlan {
@@ -1130,6 +1131,7 @@ cudaError_t reach_m(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, in
         case kModeRep16: return reach_r<LutRep<true>, PATH>(a, pl, st, per_sm);
         case kModeRep32: return reach_r<LutRep<false>, PATH>(a, pl, st, per_sm);
         case kModePart16: return reach_r<LutPart, PATH>(a, pl, st, per_sm);
+        case kModeRep16x4: return reach_r<LutRep16x4, PATH>(a, pl, st, per_sm);
         case kModePlain: return reach_r<LutPlain, PATH>(a, pl, st, per_sm);
         default: return reach_r<LutFlat, PATH>(a, pl, st, per_sm);
     }
@@ -1153,6 +1155,7 @@ cudaError_t piece_dispatch(const ReachArgs &a, const ReachPlan &pl, int sms, cud
         case kModeRep16: return piece_r<LutRep<true>>(pl.R, a, grid, smem, pl.tis, st);
         case kModeRep32: return piece_r<LutRep<false>>(pl.R, a, grid, smem, pl.tis, st);
         case kModePart16: return piece_r<LutPart>(pl.R, a, grid, smem, pl.tis, st);
+        case kModeRep16x4: return piece_r<LutRep16x4>(pl.R, a, grid, smem, pl.tis, st);
         case kModePlain: return piece_r<LutPlain>(pl.R, a, grid, smem, pl.tis, st);
         default: return piece_r<LutFlat>(pl.R, a, grid, smem, pl.tis, st);
     }
@@ -1173,18 +1176,22 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // (the half-replicated layout is only taken on request: on the codon RE, the one workload it
     // would serve, it measured slower than the compact table -- its gathers conflict less, but
     // its larger footprint leaves fewer warps and the time goes to run imbalance, not conflicts)
-    const size_t plain = LutPlain::smem_bytes(A), flat = LutFlat::smem_bytes(A);
+    const size_t plain = LutPlain::smem_bytes(A), flat = LutFlat::smem_bytes(A), rep16x4 = LutRep16x4::smem_bytes(A);
     const bool ok16 = LutRep<true>::fits16(A) && rep16 <= limit, ok32 = rep32 <= limit,
-               okp = LutPart::fits(A) && part16 <= limit, okplain = LutPlain::fits(A) && plain <= limit;
-    if (mode == 0) mode = ok16 ? kModeRep16 : ok32 ? kModeRep32 : kModePlain;
+               okp = LutPart::fits(A) && part16 <= limit, okplain = LutPlain::fits(A) && plain <= limit,
+               ok16x4 = LutRep16x4::fits(A) && rep16x4 <= limit;
+    // the scaled 16-bit table only when it still leaves room for 16 warps' staging
+    const bool roomy16x4 = ok16x4 && rep16x4 + 16 * static_cast<size_t>(kWarpCoopBytes) <= limit;
+    if (mode == 0) mode = ok16 ? kModeRep16 : ok32 ? kModeRep32 : roomy16x4 ? kModeRep16x4 : kModePlain;
+    if (mode == kModeRep16x4 && !ok16x4) return RIDFA_E_ARG;
     if (mode == kModePlain && !okplain) mode = kModeFlat;    // the compact table, through generic loads
     if ((mode == kModeRep16 && !ok16) || (mode == kModeRep32 && !ok32) || (mode == kModePart16 && !okp))
         return RIDFA_E_ARG;
-    if (mode < kModePlain || mode > kModeFlat) return RIDFA_E_ARG;
+    if (mode < kModePlain || mode > kModeRep16x4) return RIDFA_E_ARG;
     pl.mode = mode;
     pl.tis = (mode == kModeFlat && flat <= limit) ? 1 : 0;
     const size_t table_smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : mode == kModePart16 ? part16
-                              : mode == kModePlain ? plain : (pl.tis ? flat : 256);
+                              : mode == kModeRep16x4 ? rep16x4 : mode == kModePlain ? plain : (pl.tis ? flat : 256);
     const int cap = pl.R <= 4 ? 1024 : 512;
     const uint32_t text_path = tuning ? tuning->text_path : 0;
     if (text_path > 4) return RIDFA_E_ARG;
@@ -1291,13 +1298,19 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     if (piece_req > 1 && piece_req < 64) return RIDFA_E_ARG;
     uint64_t spc = 1;                                  // pieces per chunk
     if (piece_req != 1 && H.n_states >= 1 && H.n_states <= RIDFA_MAX_SLOTS) {
-        const uint64_t lanes = static_cast<uint64_t>(sms) * 1024;
-        if (c * 8 < lanes) {
+        // a piece costs a warp (1 + ceil(P/32)) lookups per byte where a chunk costs a lane 2:
+        // worth it only while the chunks would leave most of the resident warps idle
+        const uint64_t warps = static_cast<uint64_t>(sms) * 32;
+        const uint64_t rall = H.n_states <= 32 ? 1 : H.n_states <= 64 ? 2 : H.n_states <= 128 ? 4 : 8;
+        if (c * (1 + rall) * 4 <= warps) {
             const uint64_t plen = piece_req >= 64 ? piece_req : 256;
-            spc = std::min<uint64_t>(2 * lanes / c, len / (c * plen));
+            spc = std::min<uint64_t>(2 * warps * 32 / c, len / (c * plen));
             if (spc < 2) spc = 1;
         }
     }
+    // many pieces (a long text in few chunks): the reach kernel runs them, one lane per piece
+    // once its runs merge; few pieces: one lockstep warp per piece
+    const bool lockstep = spc > 1 && c * spc <= static_cast<uint64_t>(sms) * 32 * 8;
     const uint64_t pieces = c * spc;
     const uint32_t NS = H.n_states;
     Automaton Aall{D->trans, D->classmap, D->final_bits, D->ifmask, D->all_states,
@@ -1309,9 +1322,9 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     ReachPlan plan;
     err = plan_reach(ra.A, tuning, d_text, ra, sms, &plan);
     if (err != RIDFA_OK) return err;
-    // warps past the last 32-chunk task never write their run list (the piece kernel has none)
-    const uint64_t grid_warps = spc > 1 ? 0 : std::min<uint64_t>(static_cast<uint64_t>(plan.grid) * (plan.block / 32),
-                                                                 (pieces + 31) / 32);
+    // warps past the last 32-chunk task never write their run list (the lockstep kernel has none)
+    const uint64_t grid_warps = lockstep ? 0 : std::min<uint64_t>(static_cast<uint64_t>(plan.grid) * (plan.block / 32),
+                                                                  (pieces + 31) / 32);
     const uint64_t comp_funcs = spc > 1 ? c * ((spc + kComposeGroup - 1) / kComposeGroup) : 0;
     const Layout L = layout_for(c, H.k, d_maps_user == nullptr, join_blocks, grid_warps, spc > 1 ? pieces : 0,
                                 spc > 1 ? NS : 0, comp_funcs);
@@ -1344,7 +1357,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
             }
         cudaEventRecord(static_cast<cudaEvent_t>(S->ev[0]), st);
     }
-    e = spc > 1 ? piece_dispatch(ra, plan, sms, st) : reach_dispatch(ra, plan, st, nullptr);
+    e = lockstep ? piece_dispatch(ra, plan, sms, st) : reach_dispatch(ra, plan, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
     if (spc > 1) {
         // compose each chunk's piece functions, kComposeGroup per thread and level, then apply

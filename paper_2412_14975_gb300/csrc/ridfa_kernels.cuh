@@ -270,6 +270,43 @@ struct LutRep {
     }
 };
 
+// Rep16 with states in 4-byte units: the same lane-replicated table of 16-bit entries, holding
+// s' * Cp * 16 (the row offset over 4), so automata up to P * Cp <= 4095 fit the entries where
+// byte offsets would overflow them; a step is a shift-add of the state, an add of the class offset
+// and one ld.shared.u16.
+struct LutRep16x4 {
+    uint32_t lc, lt;          // shared addresses of this lane's class / transition copies
+    uint32_t row4;            // 4-byte units per state row: Cp * 16
+    __host__ __device__ static uint32_t cpad(const Automaton &A) { return (A.C + 1) & ~1u; }
+    static size_t smem_bytes(const Automaton &A) { return 256 * 128 + static_cast<size_t>(A.n + 1) * cpad(A) * 64; }
+    static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n) * cpad(A) * 16 <= 0xFFFF; }
+    __device__ __forceinline__ static uint32_t cls_off(uint32_t c) { return (c >> 1) * 128 + (c & 1) * 2; }
+    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+        const uint32_t Cp = cpad(A);
+        row4 = Cp * 16;
+        const uint32_t base_c = smem_addr(smem);
+        const uint32_t base_t = base_c + 256 * 128;
+        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x)
+            sts_u32(base_c + i * 4, cls_off(A.classmap[i >> 5]));
+        const uint32_t words = (A.n + 1) * Cp / 2;
+        for (uint32_t i = threadIdx.x; i < words * 32; i += blockDim.x) {
+            const uint32_t w = i >> 5;
+            const uint32_t s = (2 * w) / Cp, c0 = (2 * w) % Cp;
+            const uint32_t n0 = A.trans[s * A.C + c0];
+            const uint32_t n1 = (c0 + 1 < A.C) ? A.trans[s * A.C + c0 + 1] : A.n;
+            sts_u32(base_t + i * 4, (n0 * row4) | ((n1 * row4) << 16));
+        }
+        const uint32_t lane = threadIdx.x & 31;
+        lc = base_c + lane * 4;
+        lt = base_t + lane * 4;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id * row4; }
+    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s / row4; }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return lds_u16(lt + (s << 2) + c); }
+};
+
 // Half-replicated tables, for transition tables too large to replicate 32 times: the class table
 // as in LutRep (32 copies, conflict-free), the transition table in F = 16 copies, lane l reading
 // copy l & 15.  Entry (s, c) sits at byte ((s * Cp/2 + c/2) * 16 + (l & 15)) * 4 + (c & 1) * 2, so

@@ -180,6 +180,10 @@ def test_piece_speculation_maps():
                     assert np.array_equal(dmaps[i], dwant[i]), (re_src[:20], c, piece, i)
     y, _ = textgen.mutate(x3, seed=98, n_subs=3)
     check(textgen.C3_RE, y, 5, tuning=dict(piece_len=64))
+    # enough pieces (65,536) that the reach kernel runs them, one lane per piece, instead of one
+    # lockstep warp per piece
+    x4 = textgen.c3_text(4 << 20, seed=100)
+    check(textgen.C3_RE, x4, 2, tuning=dict(piece_len=64))
     re_src, xs, ys = _branches_re(40)
     rng = np.random.Generator(np.random.PCG64(99))
     parts = [xs[int(i)] + "a" * int(rng.integers(0, 300)) + ys[int(i)] for i in rng.integers(40, size=200)]
@@ -232,7 +236,7 @@ def test_text_paths_agree(path):
             assert np.array_equal(got[i], want[i])
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 6])
 def test_tuning_variants_agree(mode):
     """Every table layout (compact, lane-replicated 16/32-bit, half-replicated, generic loads) and
     launch shape gives the same bit-exact maps."""
@@ -251,8 +255,8 @@ def test_tuning_variants_agree(mode):
     z = textgen.c2_text(1 << 16, seed=79)
     # 424 states x 5 classes: the 16-bit offsets overflow and the 32-bit replicated table exceeds
     # shared memory; the compact table (automatic) and the half-replicated one (on request) fit
-    check(re2, z, 200, tuning=dict(table_mode=mode if mode in (1, 4, 5) else 0), dfa_too=False)
-    check(re2, z, 1000, tuning=dict(table_mode=mode if mode in (1, 4, 5) else 0, text_path=1), dfa_too=False)
+    check(re2, z, 200, tuning=dict(table_mode=mode if mode in (1, 4, 5, 6) else 0), dfa_too=False)
+    check(re2, z, 1000, tuning=dict(table_mode=mode if mode in (1, 4, 5, 6) else 0, text_path=1), dfa_too=False)
     prog = lib.ridfa_compile(re2)
     d = to_device(z)
     for bad in (2, 3):
