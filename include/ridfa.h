@@ -109,8 +109,9 @@ typedef struct {
                                  16-byte global loads; 2 per-lane bulk copies (cp.async.bulk)
                                  into a shared-memory ring; 3 warp-cooperative coalesced loads
                                  staged in shared memory; 4 the same with two chunks per lane,
-                                 interleaved.  2, 3 and 4 need a 16-byte-aligned d_text
-                                 (E_ARG otherwise) */
+                                 interleaved; 5 as 3, and a lane finishes all the runs its chunk
+                                 handed off in one pass over the chunk (at most 512 threads a
+                                 block).  2 to 5 need a 16-byte-aligned d_text (E_ARG otherwise) */
 } ridfa_tuning;
 
 /* Compile `re` (re_len bytes, need not be NUL-terminated) on the host: position NFA, RI-DFA

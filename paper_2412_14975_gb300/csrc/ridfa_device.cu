@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
     // per-warp staging ring and its mbarriers (bulk-copy path only)
     const uint32_t warp_in_block = threadIdx.x >> 5;
     const uint32_t stg_base = smem_addr(smem) + staging_offset +
-                              warp_in_block * (PATH == kPathCoop ? kWarpCoopBytes : kWarpStageBytes);
+                              warp_in_block * (PATH == kPathCoop || PATH == kPathCoopSet ? kWarpCoopBytes : kWarpStageBytes);
     const uint32_t bar_base = stg_base + kStages * 32 * kLaneStride;
     if (PATH == kPathBulk) {
         if ((threadIdx.x & 31) == 0)
@@ -195,10 +195,36 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
         }
         __syncwarp();
 
-        // ---------------- converged phase: each lane finishes one run (rounds of 32 runs)
+        // ---------------- converged phase: each lane finishes one run (rounds of 32 runs); when
+        // some chunk handed off several runs (staged path), each lane finishes its chunk's runs
+        // together instead
         const uint32_t total_runs = wruns ? nruns : 32;
         uint32_t fin_reg = dead;      // final state of run `lane` when there are at most 32 runs
-        for (uint32_t rb = 0; rb < total_runs; rb += 32) {
+        const bool set_path = PATH == kPathCoopSet && wruns && nruns != static_cast<uint32_t>(__popc(handed));
+        if (set_path) {
+            const uint32_t m = my_hand >> 16, run0 = my_hand & 0xFFFF;
+            uint32_t st[kMaxRun];
+            uint64_t pos = 0, end = 0;
+#pragma unroll
+            for (int g = 0; g < kMaxRun; ++g) st[g] = dead;
+            if (m) {
+#pragma unroll
+                for (int g = 0; g < kMaxRun; ++g)
+                    if (g < static_cast<int>(m)) st[g] = wruns[run0 + g].state;
+                pos = wruns[run0].pos;
+                end = chunk_begin(chunk0 + lane + 1, p.len, p.c);
+            }
+            const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
+            coop_converge_set(T, stg_base, lane, m != 0, p.text, lim, min(end, lim), pos, st, m, dead);
+#pragma unroll
+            for (int g = 0; g < kMaxRun; ++g) {
+                if (g >= static_cast<int>(m)) continue;
+                uint64_t pg = pos;
+                tail_converge<LUT, false>(T, p.text, pg, end, st[g], dead);
+                wfin[run0 + g] = st[g];
+            }
+        }
+        for (uint32_t rb = 0; rb < (set_path ? 0u : total_runs); rb += 32) {
             bool my_pending;
             uint64_t pos = 0, end = 0;
             uint32_t s = dead, jj = lane;
@@ -217,7 +243,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
                 s = one_state;
             }
             if (my_pending) end = chunk_begin(chunk0 + jj + 1, p.len, p.c);
-            if (PATH == kPathCoop && __any_sync(kFull, my_pending)) {
+            if ((PATH == kPathCoop || PATH == kPathCoopSet) && __any_sync(kFull, my_pending)) {
                 const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
                 coop_converge<LUT, true>(T, stg_base, lane, my_pending, p.text, lim, min(end, lim), pos, s, dead);
             }
@@ -320,7 +346,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
             const uint32_t m = hand >> 16, run0 = hand & 0xFFFF;
             const uint32_t src = run0 + min(lane, m - 1);     // lane g < m: run of group g
             uint32_t fin = __shfl_sync(kFull, fin_reg, src & 31);
-            if (total_runs > 32) fin = wfin[src];
+            if (total_runs > 32 || set_path) fin = wfin[src];
             uint32_t am = 0;
 #pragma unroll
             for (int r = 0; r < R; ++r) am |= ((amask[r] >> j) & 1u) << r;
@@ -1096,8 +1122,8 @@ struct ReachPlan {
     uint32_t staging_offset = 0;
 };
 
-template <int R>
-constexpr int block_cap() { return R <= 4 ? 1024 : 512; }
+template <int R, int PATH = kPathCoop>
+constexpr int block_cap() { return R <= 4 && PATH != kPathCoopSet ? 1024 : 512; }
 
 // Launch (or, with per_sm != nullptr, size) one instantiation of the reach kernel.
 template <int R>
@@ -1107,7 +1133,7 @@ template <int R, class LUT, int PATH>
 cudaError_t reach_one(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
     using KernT = void (*)(ReachArgs, int, uint32_t);
     KernT kern = PATH == kPathCoop2 ? rid_reach2_kernel<R, LUT, block_cap2<R>()>
-                                    : rid_reach_kernel<R, LUT, block_cap<R>(), PATH == kPathCoop2 ? kPathGlobal : PATH>;
+                                    : rid_reach_kernel<R, LUT, block_cap<R, PATH>(), PATH == kPathCoop2 ? kPathGlobal : PATH>;
     cudaError_t e = ensure_smem_cap(reinterpret_cast<const void *>(kern), pl.smem);
     if (e != cudaSuccess) return e;
     if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, pl.block, pl.smem);
@@ -1142,6 +1168,7 @@ cudaError_t reach_dispatch(const ReachArgs &a, const ReachPlan &pl, cudaStream_t
         case kPathBulk: return reach_m<kPathBulk>(a, pl, st, per_sm);
         case kPathCoop: return reach_m<kPathCoop>(a, pl, st, per_sm);
         case kPathCoop2: return reach_m<kPathCoop2>(a, pl, st, per_sm);
+        case kPathCoopSet: return reach_m<kPathCoopSet>(a, pl, st, per_sm);
         default: return reach_m<kPathGlobal>(a, pl, st, per_sm);
     }
 }
@@ -1198,7 +1225,7 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
                               : mode == kModeRep16x4 ? rep16x4 : mode == kModePlain ? plain : (pl.tis ? flat : 256);
     const int cap = pl.R <= 4 ? 1024 : 512;
     const uint32_t text_path = tuning ? tuning->text_path : 0;
-    if (text_path > 4) return RIDFA_E_ARG;
+    if (text_path > 5) return RIDFA_E_ARG;
     pl.staging_offset = static_cast<uint32_t>((table_smem + 127) & ~static_cast<size_t>(127));
     const size_t room = limit > pl.staging_offset ? limit - pl.staging_offset : 0;
     const bool aligned = (reinterpret_cast<uintptr_t>(text) & 15) == 0;
@@ -1213,26 +1240,38 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
         return (block == 0 ? w >= 4 : block / 32 <= w) ? w : 0;
     };
     const int w_coop = fits(kWarpCoopBytes), w_bulk = fits(kWarpStageBytes), w_coop2 = fits2(kWarpCoop2Bytes);
+    const int w_set = std::min(w_coop, 512 / 32);
     // auto: one chain per lane with cooperative staging (16-byte-aligned text, buffers fit),
     // else plain global loads.  (Two chains per lane and bulk copies measured slower on GB300.)
+    // Automata whose table is too large to replicate are the ones whose runs stay apart: there a
+    // lane finishes all of its chunk's runs together (measured on the codon RE: 1.21x; on
+    // replicated-table workloads the 512-thread cap of that variant cost 8-13%).
+    const bool many_runs = mode == kModePlain || mode == kModeFlat;
     if (text_path == 0)
-        pl.path = !aligned ? kPathGlobal : w_coop ? kPathCoop : kPathGlobal;
+        pl.path = !aligned ? kPathGlobal
+                  : !w_coop ? kPathGlobal
+                  : many_runs && w_set >= 4 && block <= 512 ? kPathCoopSet : kPathCoop;
     else if (text_path == 1) pl.path = kPathGlobal;
     else if (text_path == 2) pl.path = kPathBulk;
     else if (text_path == 3) pl.path = kPathCoop;
-    else pl.path = kPathCoop2;
+    else if (text_path == 4) pl.path = kPathCoop2;
+    else pl.path = kPathCoopSet;
     if (pl.path == kPathBulk && !(aligned && w_bulk)) return RIDFA_E_ARG;
     if (pl.path == kPathCoop && !(aligned && w_coop)) return RIDFA_E_ARG;
     if (pl.path == kPathCoop2 && !(aligned && w_coop2)) return RIDFA_E_ARG;
-    const int warps_fit = pl.path == kPathBulk    ? w_bulk
-                          : pl.path == kPathCoop  ? w_coop
+    if (pl.path == kPathCoopSet && !(aligned && w_set)) return RIDFA_E_ARG;
+    const int warps_fit = pl.path == kPathBulk      ? w_bulk
+                          : pl.path == kPathCoop    ? w_coop
+                          : pl.path == kPathCoopSet ? w_set
                           : pl.path == kPathCoop2 ? w_coop2
                                                   : cap / 32;
     if (block == 0) block = pl.path == kPathGlobal ? (mode == kModeFlat && !pl.tis ? 256 : cap) : warps_fit * 32;
-    if (block < 32 || block > (pl.path == kPathCoop2 ? cap2 : cap) || block % 32) return RIDFA_E_ARG;
+    const int bcap = pl.path == kPathCoop2 ? cap2 : pl.path == kPathCoopSet ? 512 : cap;
+    if (block < 32 || block > bcap || block % 32) return RIDFA_E_ARG;
     pl.block = block;
     pl.smem = pl.path == kPathBulk    ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpStageBytes
-              : pl.path == kPathCoop  ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpCoopBytes
+              : pl.path == kPathCoop || pl.path == kPathCoopSet
+                  ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpCoopBytes
               : pl.path == kPathCoop2 ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpCoop2Bytes
                                       : table_smem;
     const uint64_t tasks = (static_cast<uint64_t>(ra.c) + (pl.path == kPathCoop2 ? 63 : 31)) /

@@ -100,6 +100,7 @@ constexpr int kPathGlobal = 0;   // each lane: 16-byte global loads of its own c
 constexpr int kPathBulk = 1;     // each lane: 1-D bulk copies into a shared-memory ring
 constexpr int kPathCoop = 2;     // the warp: coalesced loads of 8 chunks' windows per instruction
 constexpr int kPathCoop2 = 3;    // the same with two chunks per lane, interleaved
+constexpr int kPathCoopSet = 4;  // kPathCoop, and a lane finishes all runs its chunk handed off together
 // cooperative path: one 64-byte window per chunk of the warp; granule g of chunk j's window sits
 // at 16-byte unit 4j + (g ^ ((j >> 1) & 3)), so both the stores (lanes write 4 granules of 2
 // chunks per 8-lane phase) and the owners' 16-byte reads (8 chunks, one granule each) are
@@ -632,6 +633,80 @@ __device__ __forceinline__ void coop_converge(const LUT &T, uint32_t stg_base, u
             pos = hi;
         }
         __syncwarp();                         // buffer (r & 1) is refilled next round
+    }
+    cp_async_wait0();
+    __syncwarp();
+}
+
+// coop_converge for a lane that carries all the runs of one chunk together (up to kMaxRun states
+// handed off at one position): the text is staged once per chunk and each byte's class is looked
+// up once for all of them, so m runs cost 1 + m lookups per byte instead of 2m.  Dead states stay
+// dead (the dead row maps to itself) and are skipped once a whole granule has passed.
+template <class LUT>
+__device__ __forceinline__ void coop_converge_set(const LUT &T, uint32_t stg_base, uint32_t lane, bool pending,
+                                                  const uint8_t *base, uint64_t lim, uint64_t stop, uint64_t &pos,
+                                                  uint32_t (&s)[kMaxRun], uint32_t m, uint32_t dead) {
+    const uint64_t wb = pos & ~static_cast<uint64_t>(15);
+    const uint32_t nwin = (pending && wb < stop)
+                              ? static_cast<uint32_t>((stop - wb + kCoopWin - 1) / kCoopWin) : 0;
+    const uint64_t waddr = reinterpret_cast<uint64_t>(base) + wb;
+    const uint64_t wlim = reinterpret_cast<uint64_t>(base) + lim;
+    const uint32_t g = lane & 3;
+    const uint32_t max_win = __reduce_max_sync(kFull, nwin);
+    uint32_t live = 0;
+#pragma unroll
+    for (int q = 0; q < kMaxRun; ++q)
+        if (q < static_cast<int>(m) && s[q] != dead) live |= 1u << q;
+    auto issue = [&](uint32_t r) {
+        const uint32_t buf = stg_base + (r & 1) * kCoopBufBytes;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = u * 8 + (lane >> 2);
+            const uint64_t a = __shfl_sync(kFull, waddr, j) + static_cast<uint64_t>(kCoopWin) * r + 16 * g;
+            const uint32_t nw = __shfl_sync(kFull, nwin, j);
+            const uint64_t la = __shfl_sync(kFull, wlim, j);
+            if (r < nw && a + 16 <= la) cp_async_16(buf + 16 * coop_unit(j, g), reinterpret_cast<const void *>(a));
+        }
+        cp_async_commit();
+    };
+    auto step = [&](uint32_t c) {
+#pragma unroll
+        for (int q = 0; q < kMaxRun; ++q)
+            if (live & (1u << q)) s[q] = T.next(s[q], c);
+    };
+    issue(0);
+    const uint32_t sw = (lane >> 1) & 3;
+    for (uint32_t r = 0; r < max_win; ++r) {
+        if (r + 1 < max_win) issue(r + 1);
+        else cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        const uint64_t ws = wb + static_cast<uint64_t>(kCoopWin) * r;
+        if (r < nwin && live) {
+            const uint32_t sb = stg_base + (r & 1) * kCoopBufBytes + 64 * lane;
+            const uint64_t lo = max(pos, ws), hi = min(stop, ws + kCoopWin);
+            if (lo == ws && hi == ws + kCoopWin) {
+#pragma unroll
+                for (uint32_t q16 = 0; q16 < kCoopWin / 16; ++q16) {
+                    const uint4 x = lds_v4(sb + 16 * (q16 ^ sw));
+                    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) step(T.cls_at(w[q >> 2], q & 3));
+                    uint32_t nl = 0;
+#pragma unroll
+                    for (int q = 0; q < kMaxRun; ++q)
+                        if ((live & (1u << q)) && s[q] != dead) nl |= 1u << q;
+                    live = nl;
+                }
+            } else {
+                for (uint64_t q = lo; q < hi; ++q) {
+                    const uint32_t o = static_cast<uint32_t>(q - ws);
+                    step(T.cls_of(lds_u8(sb + 16 * ((o >> 4) ^ sw) + (o & 15))));
+                }
+            }
+            pos = hi;
+        }
+        __syncwarp();
     }
     cp_async_wait0();
     __syncwarp();

@@ -203,13 +203,13 @@ def test_multi_run_handoff_rows():
     re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
     x = textgen.c2_text((1 << 20) + 13, seed=91)
     for c in (1000, 3001):
-        for path in (1, 2, 3):
+        for path in (1, 2, 3, 5):
             check(re2, x, c, dfa_too=False, rows=list(range(c)), tuning=dict(text_path=path))
     y, _ = textgen.mutate(x, seed=92, n_subs=3, alphabet=b"ACGT")
     check(re2, y, 1000, dfa_too=False, rows=list(range(1000)))
 
 
-@pytest.mark.parametrize("path", [1, 2, 3, 4])
+@pytest.mark.parametrize("path", [1, 2, 3, 4, 5])
 def test_text_paths_agree(path):
     """16-byte global loads and bulk-copy staging give the same maps, on aligned texts and on
     texts that start 1..15 bytes past an alignment boundary (bulk copies then refuse)."""
@@ -222,7 +222,7 @@ def test_text_paths_agree(path):
     for off in (1, 3, 8, 15):
         y = x[off:]
         d = base[16 + off:]
-        if path in (2, 3, 4):
+        if path in (2, 3, 4, 5):
             with pytest.raises(lib.RidfaError) as e:
                 lib.ridfa_recognize(prog, d, y.size, 100, tuning=dict(text_path=path))
             assert e.value.code == -1
@@ -246,7 +246,8 @@ def test_tuning_variants_agree(mode):
               dict(block_threads=1024), dict(), dict(text_path=2, block_threads=128),
               dict(text_path=2, grid_blocks=2), dict(text_path=1, block_threads=1024),
               dict(text_path=3, block_threads=96), dict(text_path=3, grid_blocks=1),
-              dict(text_path=4, block_threads=64), dict(text_path=4, grid_blocks=1), dict(text_path=4)]:
+              dict(text_path=4, block_threads=64), dict(text_path=4, grid_blocks=1), dict(text_path=4),
+              dict(text_path=5), dict(text_path=5, block_threads=160, grid_blocks=2)]:
         t["table_mode"] = mode
         check(textgen.C3_RE, x, 1000, dfa_too=True, tuning=t)
     y = textgen.c1_text(1 << 16, seed=78)
