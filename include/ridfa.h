@@ -218,6 +218,17 @@ int ridfa_recognize(const ridfa_program *prog, const uint8_t *d_text, size_t len
                     uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *h_accept,
                     uint16_t *d_chunk_maps, void *stream);
 
+/* Recognize one text held in host memory: the len bytes at h_text are copied to the caller's
+ * device buffer d_staging (at least len bytes; 16-byte aligned for the staged text paths) on
+ * `stream`, then recognized as by ridfa_recognize; the accept bit comes back in *h_accept.
+ * h_text may be page-locked (a direct copy at the link's rate) or pageable (staged by the
+ * driver).  Ownership: both buffers stay the caller's; d_staging holds the text afterwards.
+ * Synchronises `stream`.  Errors: as ridfa_recognize; E_ARG also for a null h_text or d_staging
+ * with len > 0. */
+int ridfa_recognize_host(const ridfa_program *prog, const uint8_t *h_text, size_t len,
+                         uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *d_staging,
+                         uint8_t *h_accept, void *stream);
+
 /* As ridfa_recognize, but the accept byte goes to device memory d_accept (1 byte) and nothing
  * is synchronised: the result is valid once `stream` reaches this point.  Device status
  * (E_STATE) is then reported by the next call on the program, or by ridfa_last_status(). */

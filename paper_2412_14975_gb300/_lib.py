@@ -61,6 +61,7 @@ _decl("ridfa_delegates", _c.c_int, [_vp, _vp])
 _decl("ridfa_export_tables", _c.c_int, [_vp, _c.c_int, _vp, _vp, _vp])
 for _n in ("ridfa_recognize", "ridfa_recognize_async", "ridfa_recognize_dfa", "ridfa_recognize_dfa_async"):
     _decl(_n, _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _c.POINTER(Tuning), _vp, _vp, _vp])
+_decl("ridfa_recognize_host", _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _c.POINTER(Tuning), _vp, _vp, _vp])
 _decl("ridfa_last_status", _c.c_int, [_vp, _vp])
 _decl("ridfa_recognize_noalloc", _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _vp, _vp, _vp])
 _decl("ridfa_bench_smem_gather", _c.c_int, [_u32, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)])
@@ -226,6 +227,19 @@ def ridfa_recognize(prog, d_text, length, n_chunks, tuning=None, d_chunk_maps=No
     """Accept bit of the text (device buffer) by the RID; synchronises the stream."""
     return _recognize_sync(_lib.ridfa_recognize, "ridfa_recognize", prog, d_text, length,
                            n_chunks, tuning, d_chunk_maps, stream)
+
+
+def ridfa_recognize_host(prog, h_text, length, n_chunks, d_staging, tuning=None, stream=None):
+    """Accept bit of a text in host memory (a page-locked CPU tensor, a numpy array or a bytes-like
+    object), copied by the library into the device buffer d_staging and recognized there;
+    synchronises the stream."""
+    if isinstance(h_text, (bytes, bytearray, memoryview)):
+        h_text = np.frombuffer(h_text, dtype=np.uint8)
+    acc = _c.c_uint8(0)
+    _check(_lib.ridfa_recognize_host(prog, _ptr(h_text), int(length), int(n_chunks), _tuning(tuning),
+                                     _ptr(d_staging), _c.addressof(acc), _stream(stream)),
+           "ridfa_recognize_host")
+    return bool(acc.value)
 
 
 def ridfa_recognize_async(prog, d_text, length, n_chunks, d_accept, tuning=None,

@@ -1524,6 +1524,18 @@ extern "C" int ridfa_recognize(const ridfa_program *prog, const uint8_t *d_text,
                                  d_chunk_maps, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" int ridfa_recognize_host(const ridfa_program *prog, const uint8_t *h_text, size_t len,
+                                    uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *d_staging,
+                                    uint8_t *h_accept, void *stream) {
+    if (!prog || !h_accept || (len && (!h_text || !d_staging))) return RIDFA_E_ARG;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (len) {
+        const cudaError_t e = cudaMemcpyAsync(d_staging, h_text, len, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return ridfa::cuda_fail(e);
+    }
+    return ridfa::recognize_impl(prog, false, d_staging, len, n_chunks, tuning, nullptr, h_accept, nullptr, st);
+}
+
 extern "C" int ridfa_recognize_async(const ridfa_program *prog, const uint8_t *d_text, size_t len,
                                      uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *d_accept,
                                      uint16_t *d_chunk_maps, void *stream) {
