@@ -105,7 +105,11 @@ __device__ __forceinline__ uint32_t first_text(const ProgDesc &P, uint64_t ch) {
     return lo;
 }
 
-template <int R, class LUT, int BLOCK, bool COOP>
+// How a batch reach launch's converged runs read the text: plain 16-byte global loads, warp-
+// cooperative staging, or staging with each lane finishing all the runs its chunk handed off.
+constexpr int kTpGlobal = 0, kTpCoop = 1, kTpSet = 2;
+
+template <int R, class LUT, int BLOCK, int TP>
 __global__ void __launch_bounds__(BLOCK, 1) rid_reach_batch_kernel(BatchReachArgs b, uint32_t staging_offset) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint32_t s_task;
@@ -176,9 +180,38 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_batch_kernel(BatchReachArg
 #pragma unroll
             for (int r = 0; r < R; ++r) wball[r * 32 + lane] = amask[r];
             __syncwarp();
-            // ---- converged phase: each lane finishes one run (rounds of 32 runs)
+            // ---- converged phase: each lane finishes one run (rounds of 32 runs); on the set
+            // path, when some chunk handed off several runs, each lane finishes its chunk's runs
+            // together
             uint32_t fin_reg = dead;
-            for (uint32_t rb = 0; rb < nruns; rb += 32) {
+            const bool set_path = TP == kTpSet && nruns != static_cast<uint32_t>(__popc(handed));
+            if (set_path) {
+                const uint32_t m = my_hand >> 16, run0 = my_hand & 0xFFFF;
+                uint32_t stv[kMaxRun];
+                uint64_t pos = 0, end = 0, lim = 0;
+                const uint8_t *tx = nullptr;
+#pragma unroll
+                for (int g = 0; g < kMaxRun; ++g) stv[g] = dead;
+                if (m) {
+#pragma unroll
+                    for (int g = 0; g < kMaxRun; ++g)
+                        if (g < static_cast<int>(m)) stv[g] = wruns[run0 + g].state;
+                    pos = wruns[run0].pos;
+                    const TextDesc &td = P.texts[my_ti];
+                    end = chunk_begin(c0 + lane - td.chunk_base + 1, td.len, td.c);
+                    lim = td.len & ~static_cast<uint64_t>(15);
+                    tx = td.text;
+                }
+                coop_converge_set(T, stg_base, lane, m != 0, tx, lim, min(end, lim), pos, stv, m, dead);
+#pragma unroll
+                for (int g = 0; g < kMaxRun; ++g) {
+                    if (g >= static_cast<int>(m)) continue;
+                    uint64_t pg = pos;
+                    tail_converge<LUT, false>(T, tx, pg, end, stv[g], dead);
+                    wfin[run0 + g] = stv[g];
+                }
+            }
+            for (uint32_t rb = 0; rb < (set_path ? 0u : nruns); rb += 32) {
                 const uint32_t idx = rb + lane;
                 const bool pending = idx < nruns;
                 uint64_t pos = 0, end = 0, lim = 0;
@@ -197,10 +230,10 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_batch_kernel(BatchReachArg
                     lim = td.len & ~static_cast<uint64_t>(15);
                     tx = td.text;
                 }
-                if (COOP && __any_sync(kFull, pending))
+                if (TP != kTpGlobal && __any_sync(kFull, pending))
                     coop_converge<LUT, false>(T, stg_base, lane, pending, tx, lim, min(end, lim), pos, s, dead);
                 if (pending) {
-                    tail_converge<LUT, !COOP>(T, tx, pos, end, s, dead);
+                    tail_converge<LUT, TP == kTpGlobal>(T, tx, pos, end, s, dead);
                     if (nruns > 32) wfin[idx] = s;
                     else fin_reg = s;
                 }
@@ -215,7 +248,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_batch_kernel(BatchReachArg
                 const uint32_t m = hand >> 16, run0 = hand & 0xFFFF;
                 const uint32_t src = run0 + min(lane, m - 1);
                 uint32_t fin = __shfl_sync(kFull, fin_reg, src & 31);
-                if (nruns > 32) fin = wfin[src];
+                if (nruns > 32 || set_path) fin = wfin[src];
                 uint32_t am = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) am |= ((amask[r] >> j) & 1u) << r;
@@ -437,7 +470,7 @@ enum BMode : uint32_t { kBPlain = 1, kBRep16 = 2, kBRep32 = 3, kBFlat = 4, kBRep
 struct LaunchGroup {          // one persistent reach launch
     uint32_t mode = kBPlain;
     int R = 1;
-    bool coop = false;
+    int tp = kTpGlobal;            // how converged runs read the text
     std::vector<uint32_t> progs;   // batch program indices in this launch
     uint32_t task0 = 0, n_tasks = 0;
     size_t table_smem = 0;
@@ -447,10 +480,10 @@ struct LaunchGroup {          // one persistent reach launch
     size_t smem = 0;               // dynamic shared memory
 };
 
-template <int R, class LUT, bool COOP>
+template <int R, class LUT, int TP>
 cudaError_t batch_reach_one(const BatchReachArgs &a, int grid, int block, size_t smem, uint32_t stg,
                             cudaStream_t st, int *per_sm) {
-    auto kern = rid_reach_batch_kernel<R, LUT, (R <= 4 ? 1024 : 512), COOP>;
+    auto kern = rid_reach_batch_kernel<R, LUT, (R <= 4 && TP != kTpSet ? 1024 : 512), TP>;
     cudaError_t e = ensure_smem_cap(reinterpret_cast<const void *>(kern), smem);
     if (e != cudaSuccess) return e;
     if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, block, smem);
@@ -458,42 +491,38 @@ cudaError_t batch_reach_one(const BatchReachArgs &a, int grid, int block, size_t
     return cudaGetLastError();
 }
 
-template <class LUT, bool COOP>
+template <class LUT, int TP>
 cudaError_t batch_reach_r(int R, const BatchReachArgs &a, int grid, int block, size_t smem, uint32_t stg,
                           cudaStream_t st, int *per_sm) {
     switch (R) {
-        case 1: return batch_reach_one<1, LUT, COOP>(a, grid, block, smem, stg, st, per_sm);
-        case 2: return batch_reach_one<2, LUT, COOP>(a, grid, block, smem, stg, st, per_sm);
-        case 4: return batch_reach_one<4, LUT, COOP>(a, grid, block, smem, stg, st, per_sm);
-        default: return batch_reach_one<8, LUT, COOP>(a, grid, block, smem, stg, st, per_sm);
+        case 1: return batch_reach_one<1, LUT, TP>(a, grid, block, smem, stg, st, per_sm);
+        case 2: return batch_reach_one<2, LUT, TP>(a, grid, block, smem, stg, st, per_sm);
+        case 4: return batch_reach_one<4, LUT, TP>(a, grid, block, smem, stg, st, per_sm);
+        default: return batch_reach_one<8, LUT, TP>(a, grid, block, smem, stg, st, per_sm);
     }
 }
 
 cudaError_t batch_reach(const LaunchGroup &g, const BatchReachArgs &a, cudaStream_t st, int *per_sm) {
-    if (g.coop) {
-        switch (g.mode) {
-            case kBRep16: return batch_reach_r<LutRep<true>, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-            case kBRep32: return batch_reach_r<LutRep<false>, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-            case kBPlain: return batch_reach_r<LutPlain, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-            case kBRep16x4: return batch_reach_r<LutRep16x4, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-            default: return batch_reach_r<LutFlat, true>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-        }
+#define RIDFA_BATCH_MODES(TPV)                                                                                  \
+    switch (g.mode) {                                                                                           \
+        case kBRep16: return batch_reach_r<LutRep<true>, TPV>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);  \
+        case kBRep32: return batch_reach_r<LutRep<false>, TPV>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm); \
+        case kBPlain: return batch_reach_r<LutPlain, TPV>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);      \
+        case kBRep16x4: return batch_reach_r<LutRep16x4, TPV>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);  \
+        default: return batch_reach_r<LutFlat, TPV>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);           \
     }
-    switch (g.mode) {
-        case kBRep16: return batch_reach_r<LutRep<true>, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-        case kBRep32: return batch_reach_r<LutRep<false>, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-        case kBPlain: return batch_reach_r<LutPlain, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-        case kBRep16x4: return batch_reach_r<LutRep16x4, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-        default: return batch_reach_r<LutFlat, false>(g.R, a, g.grid, g.block, g.smem, g.stg, st, per_sm);
-    }
+    if (g.tp == kTpSet) { RIDFA_BATCH_MODES(kTpSet) }
+    if (g.tp == kTpCoop) { RIDFA_BATCH_MODES(kTpCoop) }
+    RIDFA_BATCH_MODES(kTpGlobal)
+#undef RIDFA_BATCH_MODES
 }
 
 // Resident blocks per SM of a launch group's kernel, cached: setting the shared-memory attribute
 // and querying occupancy once per (device, layout, R, path, block, shared memory).
 int blocks_per_sm(int device, const LaunchGroup &g, int *per_sm) {
     static std::mutex mu;
-    static std::map<std::tuple<int, uint32_t, int, bool, int, size_t>, int> cache;
-    const auto key = std::make_tuple(device, g.mode, g.R, g.coop, g.block, g.smem);
+    static std::map<std::tuple<int, uint32_t, int, int, int, size_t>, int> cache;
+    const auto key = std::make_tuple(device, g.mode, g.R, g.tp, g.block, g.smem);
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
     if (it != cache.end()) {
@@ -629,7 +658,9 @@ int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, co
     for (uint32_t m = kBPlain; m <= kBRep16x4; ++m) {
         LaunchGroup g;
         g.mode = m;
-        g.coop = aligned_all;
+        // staged text when every text is 16-byte aligned; tables too large to replicate (their
+        // runs stay apart) finish a chunk's runs together, at up to 512 threads
+        g.tp = !aligned_all ? kTpGlobal : (m == kBPlain || m == kBFlat) ? kTpSet : kTpCoop;
         for (uint32_t p = 0; p < np; ++p)
             if (mode[p] == m && prog_chunks[p]) {
                 g.progs.push_back(p);
@@ -639,12 +670,12 @@ int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, co
             }
         if (g.progs.empty()) continue;
         g.task0 = static_cast<uint32_t>(P.tasks.size());
-        const int cap = g.R <= 4 ? 1024 : 512;
+        const int cap = g.R <= 4 && g.tp != kTpSet ? 1024 : 512;
         g.stg = static_cast<uint32_t>((g.table_smem + 127) & ~static_cast<size_t>(127));
-        int warps = g.coop ? static_cast<int>(std::min<size_t>(cap / 32, (limit - g.stg) / kWarpCoopBytes)) : cap / 32;
+        int warps = g.tp != kTpGlobal ? static_cast<int>(std::min<size_t>(cap / 32, (limit - g.stg) / kWarpCoopBytes)) : cap / 32;
         warps = std::max(warps, 1);
         g.block = warps * 32;
-        g.smem = g.coop ? g.stg + static_cast<size_t>(warps) * kWarpCoopBytes : g.table_smem;
+        g.smem = g.tp != kTpGlobal ? g.stg + static_cast<size_t>(warps) * kWarpCoopBytes : g.table_smem;
         const uint64_t per_task = 32ull * warps;
         for (uint32_t p : g.progs)
             for (uint64_t c0 = 0; c0 < prog_chunks[p]; c0 += per_task)

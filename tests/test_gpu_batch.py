@@ -137,3 +137,58 @@ def test_recognize_batch_one_shot_and_errors():
     with pytest.raises(lib.RidfaError) as e:
         lib.ridfa_batch_create(progs, [(d, 10, 0, 11)], acc)
     assert e.value.code == -4
+
+
+ORF_RE = "(([ACGT]{3})*ATG([ACGT]{3}){2,6}(TAA|TAG|TGA))*"   # 825 RI-DFA states: compact table
+
+
+def orf_text(n, rng):
+    """Concatenated open reading frames (random codons, ATG, 2-6 codons, a stop codon) of about n
+    bytes: a word of ORF_RE, whose reading frame (length mod 3) every chunk must carry."""
+    codons = [a + b + c for a in "ACGT" for b in "ACGT" for c in "ACGT"]
+    parts, tot = [], 0
+    while tot < n:
+        s = "".join(rng.choice(codons, int(rng.integers(0, 12)))) + "ATG" + \
+            "".join(rng.choice(codons, int(rng.integers(2, 7)))) + str(rng.choice(["TAA", "TAG", "TGA"]))
+        parts.append(s)
+        tot += len(s)
+    return np.frombuffer("".join(parts).encode(), dtype=np.uint8)
+
+
+@pytest.mark.parametrize("aligned", [True, False])
+def test_batch_compact_table_reading_frame(aligned):
+    """A program whose table is too large to replicate (runs stay apart; on aligned texts each
+    lane finishes all of its chunk's runs together) and whose accept bit depends on every chunk's
+    end states: positives, one-byte deletions (frame broken, rejected) and substitutions."""
+    rng = np.random.Generator(np.random.PCG64(41 if aligned else 42))
+    prog = lib.ridfa_compile(ORF_RE)
+    ser = SerialRecognizer(ORF_RE)
+    texts = []
+    for i in range(48):
+        x = orf_text(int(rng.choice([200, 3000, 20_000, 60_000])), rng)
+        if i % 3 == 1:
+            j = int(rng.integers(x.size))
+            x = np.concatenate([x[:j], x[j + 1:]])
+        elif i % 3 == 2:
+            x = x.copy()
+            x[int(rng.integers(x.size))] = ord("ACGT"[int(rng.integers(4))])
+        texts.append(np.ascontiguousarray(x))
+    want = np.array([ser.accepts(x) for x in texts])
+    assert want.any() and not want.all()
+    offs, pos = [], 0
+    for i, x in enumerate(texts):
+        pos = ((pos + 15) & ~15) + (0 if aligned or i % 2 == 0 else 3)
+        offs.append(pos)
+        pos += x.size
+    buf = np.zeros(pos, np.uint8)
+    for o, x in zip(offs, texts):
+        buf[o:o + x.size] = x
+    d = torch.from_numpy(buf).to("cuda:0")
+    items = [(d.data_ptr() + o, x.size, 0, 0) for o, x in zip(offs, texts)]
+    for chunk_len in (512, 2048):
+        acc = torch.full((len(items),), 7, dtype=torch.uint8, device="cuda:0")
+        b = lib.ridfa_batch_create([prog], items, acc, chunk_len=chunk_len)
+        lib.ridfa_batch_run(b)
+        torch.cuda.synchronize()
+        assert np.array_equal(acc.cpu().numpy().astype(bool), want), chunk_len
+        b.close()

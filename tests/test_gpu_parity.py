@@ -288,3 +288,47 @@ def test_c3_64mib_sampled_rows():
     assert check(textgen.C3_RE, x, c, rows=rows)
     y, _ = textgen.mutate(x, seed=5, n_subs=3)
     check(textgen.C3_RE, y, c, rows=rows)
+
+
+def test_recognize_host_buffers():
+    """Texts in host memory (pageable numpy, bytes, page-locked tensor) go through the one-call
+    host entry: copied into the caller's device buffer and recognized; the accept bit and the
+    staged bytes match the oracle and the source.  Empty text and null buffers."""
+    x = textgen.c3_text((1 << 20) + 5, seed=101)
+    y, _ = textgen.mutate(x, seed=102, n_subs=2)
+    prog = lib.ridfa_compile(textgen.C3_RE)
+    _, ser = oracle(textgen.C3_RE)
+    d_stage = torch.empty(x.size + 16, dtype=torch.uint8, device="cuda:0")
+    for t in (x, y):
+        want = ser.accepts(t)
+        for c in (1, 64, 1000):
+            assert lib.ridfa_recognize_host(prog, t, t.size, c, d_stage) is want
+        assert lib.ridfa_recognize_host(prog, t.tobytes(), t.size, 77, d_stage) is want
+        pinned = torch.from_numpy(t.copy()).pin_memory()
+        assert lib.ridfa_recognize_host(prog, pinned, t.size, 155, d_stage) is want
+        assert np.array_equal(d_stage[:t.size].cpu().numpy(), t)
+    eps = lib.ridfa_compile("a*")
+    assert lib.ridfa_recognize_host(eps, None, 0, 0, None) is True
+    for bad in [(None, 10, 1, d_stage), (x, 10, 1, None)]:
+        with pytest.raises(lib.RidfaError) as e:
+            lib.ridfa_recognize_host(prog, *bad)
+        assert e.value.code == -1
+
+
+def test_compact_table_runs_finished_together():
+    """Every row of a program with a compact (unreplicated) table, where chunks hand off several
+    runs: the automatic path (each lane finishes its chunk's runs together) and one run per lane
+    give the oracle's maps."""
+    re_src = "(([ACGT]{3})*ATG([ACGT]{3}){2,6}(TAA|TAG|TGA))*"
+    rng = np.random.Generator(np.random.PCG64(103))
+    codons = [a + b + c for a in "ACGT" for b in "ACGT" for c in "ACGT"]
+    parts = []
+    while sum(map(len, parts)) < 24_000:
+        parts.append("".join(rng.choice(codons, int(rng.integers(0, 12)))) + "ATG" +
+                     "".join(rng.choice(codons, int(rng.integers(2, 7)))) + "TGA")
+    x = np.frombuffer("".join(parts).encode(), dtype=np.uint8)
+    y = np.concatenate([x[:5000], x[5001:]])
+    for t in (x, y):
+        for c in (23, 100):
+            for tuning in (None, dict(text_path=3), dict(text_path=5, block_threads=64)):
+                check(re_src, t, c, dfa_too=False, rows=list(range(c)), tuning=tuning)
