@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
             uint32_t d, alive[R];
             uint64_t hp = 0;
             const int m = speculate<R, LUT>(T, A, p.text, beg, end, p.probe, lane, start_state, start_live, dead,
-                                            p.maps + ch * A.k, p.dinfo + ch, p.status, wruns != nullptr,
+                                            p.maps + ch * p.stride, p.dinfo + ch, p.status, wruns != nullptr,
                                             wruns == nullptr, &hp, &d, alive);
             if (m >= 1) {
                 handed |= 1u << j;
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
             uint32_t am = 0;
 #pragma unroll
             for (int r = 0; r < R; ++r) am |= ((amask[r] >> j) & 1u) << r;
-            finish_handed_row<R, LUT>(T, p.maps + (chunk0 + j) * A.k, A.k, m, m >= 2 || !wball, lane, am, fin,
+            finish_handed_row<R, LUT>(T, p.maps + (chunk0 + j) * p.stride, A.k, m, m >= 2 || !wball, lane, am, fin,
                                       dead, p.dinfo + chunk0 + j);
         }
     }
@@ -367,7 +367,7 @@ __device__ __forceinline__ bool speculate_chunk(const ReachArgs &p, const LUT &T
                                                 uint32_t start_live, uint32_t dead, uint64_t *out_pos,
                                                 uint32_t *out_state, uint32_t (&alive)[R]) {
     return speculate_range<R, LUT>(T, p.A, p.text, chunk_begin(ch, p.len, p.c), chunk_begin(ch + 1, p.len, p.c),
-                                   p.probe, lane, start_state, start_live, dead, p.maps + ch * p.A.k,
+                                   p.probe, lane, start_state, start_live, dead, p.maps + ch * p.stride,
                                    p.dinfo + ch, p.status, out_pos, out_state, alive);
 }
 
@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach2_kernel(ReachArgs p, int t
             for (int r = 0; r < R; ++r) any |= alive[nb][r] != 0;
             const uint32_t sid = T.id(s[nb]);
             const uint16_t val = s[nb] == dead ? kUndef : static_cast<uint16_t>(sid);
-            write_row<R>(p.maps + ch * A.k, A.k, alive[nb], val);
+            write_row<R>(p.maps + ch * p.stride, A.k, alive[nb], val);
             p.dinfo[ch] = (any && s[nb] != dead) ? ((1u << 16) | sid) : static_cast<uint32_t>(kUndef);
         }
     }
@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(256) rid_piece_kernel(ReachArgs p, int table_i
             live &= nl;
         }
         while (pos < end && live) step(__ldg(p.text + pos++));
-        uint16_t *row = p.maps + j * A.k;
+        uint16_t *row = p.maps + j * p.stride;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const uint32_t a = r * 32 + lane;
@@ -993,6 +993,8 @@ cudaError_t piece_r(int R, const ReachArgs &a, int grid, size_t smem, int tis, c
 // δ(x, y_i) = f_s(...f_1(x)) because the automaton is deterministic; the chunk's map row is that
 // composition applied to the interface slots' start states.  Exact, whatever the convergence.
 constexpr uint32_t kComposeGroup = 32;     // functions composed per thread and level
+constexpr uint32_t kMaxPieceGroups = 4;    // pieces for automata of up to 4 x 256 states
+constexpr uint64_t kManyPieceLen = 1024;   // shortest piece of the many-pieces path (bytes)
 
 // One level: function g of chunk i = the composition, in order, of input functions
 // [g*G, (g+1)*G) of that chunk.  One thread per (chunk, group, start state).
@@ -1336,38 +1338,58 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
                (static_cast<uint64_t>(kJoinThreads) * per_thread)));
     Automaton A{D->trans, D->classmap, D->final_bits, D->ifmask, D->slot_state,
                 H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
-    // intra-chunk speculation: too few chunks to fill the GPU, each long enough to cut into pieces
+    // intra-chunk speculation: too few chunks to fill the GPU, each long enough to cut into pieces.
+    // Pieces run from every state; automata of more than 256 states run theirs in groups of at
+    // most 256 states (one reach launch per group into one row of all states).
     const uint32_t piece_req = tuning ? tuning->piece_len : 0;
     if (piece_req > 1 && piece_req < 64) return RIDFA_E_ARG;
+    const uint32_t NS = H.n_states;
+    const uint32_t groups = (NS + RIDFA_MAX_SLOTS - 1) / RIDFA_MAX_SLOTS;
     uint64_t spc = 1;                                  // pieces per chunk
-    if (piece_req != 1 && H.n_states >= 1 && H.n_states <= RIDFA_MAX_SLOTS) {
-        // a piece costs a warp (1 + ceil(P/32)) lookups per byte where a chunk costs a lane 2:
-        // worth it only while the chunks would leave most of the resident warps idle
-        const uint64_t warps = static_cast<uint64_t>(sms) * 32;
-        const uint64_t rall = H.n_states <= 32 ? 1 : H.n_states <= 64 ? 2 : H.n_states <= 128 ? 4 : 8;
-        if (c * (1 + rall) * 4 <= warps) {
+    if (piece_req != 1 && NS >= 1 && groups <= kMaxPieceGroups) {
+        const uint64_t warps = static_cast<uint64_t>(sms) * 32, lanes = warps * 32;
+        const uint64_t rall = NS <= 32 ? 1 : NS <= 64 ? 2 : NS <= 128 ? 4 : 8;
+        // a short text: a lockstep piece costs a warp (1 + ceil(P/32)) lookups per byte where a
+        // chunk costs a lane 2, worth it only while the chunks leave most resident warps idle
+        if (groups == 1 && c * (1 + rall) * 4 <= warps) {
             const uint64_t plen = piece_req >= 64 ? piece_req : 256;
-            spc = std::min<uint64_t>(2 * warps * 32 / c, len / (c * plen));
-            if (spc < 2) spc = 1;
+            spc = std::min<uint64_t>(2 * lanes / c, len / (c * plen));
         }
+        // a long text in chunks that fill at most half of the lanes (a quarter per state group when
+        // the states run in groups, whose launches repeat the merged runs): pieces through the
+        // reach kernel, at most one per lane, at least kManyPieceLen bytes each
+        if (spc < 2 && c * (groups == 1 ? 2 : 4 * groups) <= lanes) {
+            const uint64_t plen = piece_req >= 64 ? piece_req : kManyPieceLen;
+            spc = std::min<uint64_t>(lanes / c, len / (c * plen));
+        }
+        if (spc < 2) spc = 1;
     }
     // many pieces (a long text in few chunks): the reach kernel runs them, one lane per piece
     // once its runs merge; few pieces: one lockstep warp per piece
-    const bool lockstep = spc > 1 && c * spc <= static_cast<uint64_t>(sms) * 32 * 8;
+    const bool lockstep = spc > 1 && groups == 1 && c * spc <= static_cast<uint64_t>(sms) * 32 * 8;
     const uint64_t pieces = c * spc;
-    const uint32_t NS = H.n_states;
-    Automaton Aall{D->trans, D->classmap, D->final_bits, D->ifmask, D->all_states,
-                   H.n_states, H.n_classes, NS, (NS + 31) / 32, 0};
-    // plan the reach launch first: the run-list scratch is sized by its grid
-    ReachArgs ra{spc > 1 ? Aall : A, d_text, len, static_cast<uint32_t>(pieces), nullptr, nullptr, nullptr, 8,
-                 nullptr, nullptr};
-    if (tuning && tuning->probe_interval) ra.probe = tuning->probe_interval;
-    ReachPlan plan;
-    err = plan_reach(ra.A, tuning, d_text, ra, sms, &plan);
-    if (err != RIDFA_OK) return err;
-    // warps past the last 32-chunk task never write their run list (the lockstep kernel has none)
-    const uint64_t grid_warps = lockstep ? 0 : std::min<uint64_t>(static_cast<uint64_t>(plan.grid) * (plan.block / 32),
-                                                                  (pieces + 31) / 32);
+    const uint32_t n_launch = spc > 1 ? groups : 1;
+    // plan the reach launches first: the run-list scratch is sized by their grids
+    ReachArgs ras[kMaxPieceGroups];
+    ReachPlan plans[kMaxPieceGroups];
+    uint64_t grid_warps = 0;
+    for (uint32_t g = 0; g < n_launch; ++g) {
+        const uint32_t kg = spc > 1 ? std::min<uint32_t>(RIDFA_MAX_SLOTS, NS - g * RIDFA_MAX_SLOTS) : H.k;
+        const Automaton Ag = spc > 1 ? Automaton{D->trans, D->classmap, D->final_bits, D->ifmask,
+                                                 D->all_states + g * RIDFA_MAX_SLOTS, H.n_states, H.n_classes,
+                                                 kg, (kg + 31) / 32, 0}
+                                     : A;
+        ras[g] = ReachArgs{Ag, d_text, len, static_cast<uint32_t>(pieces), nullptr, nullptr, nullptr, 8,
+                           nullptr, nullptr, spc > 1 ? NS : H.k};
+        if (tuning && tuning->probe_interval) ras[g].probe = tuning->probe_interval;
+        err = plan_reach(ras[g].A, tuning, d_text, ras[g], sms, &plans[g]);
+        if (err != RIDFA_OK) return err;
+        // warps past the last 32-chunk task never write their run list (the lockstep kernel has none)
+        if (!lockstep)
+            grid_warps = std::max<uint64_t>(grid_warps, std::min<uint64_t>(static_cast<uint64_t>(plans[g].grid) *
+                                                                               (plans[g].block / 32),
+                                                                           (pieces + 31) / 32));
+    }
     const uint64_t comp_funcs = spc > 1 ? c * ((spc + kComposeGroup - 1) / kComposeGroup) : 0;
     const Layout L = layout_for(c, H.k, d_maps_user == nullptr, join_blocks, grid_warps, spc > 1 ? pieces : 0,
                                 spc > 1 ? NS : 0, comp_funcs);
@@ -1381,11 +1403,15 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     uint32_t *dinfo = reinterpret_cast<uint32_t *>(base + L.dinfo_off);
     uint32_t *partials = reinterpret_cast<uint32_t *>(base + L.partials_off);
     uint32_t *piece_status = status + 1;
-    ra.maps = spc > 1 ? reinterpret_cast<uint16_t *>(base + L.pmaps_off) : maps;
-    ra.dinfo = spc > 1 ? reinterpret_cast<uint32_t *>(base + L.pdinfo_off) : dinfo;
-    ra.status = spc > 1 ? piece_status : status;
-    ra.runs = reinterpret_cast<RunEntry *>(base + L.runs_off);
-    ra.finals = reinterpret_cast<uint32_t *>(base + L.finals_off);
+    uint16_t *pmaps = reinterpret_cast<uint16_t *>(base + L.pmaps_off);
+    for (uint32_t g = 0; g < n_launch; ++g) {
+        ReachArgs &ra = ras[g];
+        ra.maps = spc > 1 ? pmaps + g * RIDFA_MAX_SLOTS : maps;
+        ra.dinfo = spc > 1 ? reinterpret_cast<uint32_t *>(base + L.pdinfo_off) : dinfo;
+        ra.status = spc > 1 ? piece_status : status;
+        ra.runs = reinterpret_cast<RunEntry *>(base + L.runs_off);
+        ra.finals = reinterpret_cast<uint32_t *>(base + L.finals_off);
+    }
     e = cudaMemsetAsync(status, 0, 8, st);
     if (e != cudaSuccess) return cuda_fail(e);
 
@@ -1400,12 +1426,15 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
             }
         cudaEventRecord(static_cast<cudaEvent_t>(S->ev[0]), st);
     }
-    e = lockstep ? piece_dispatch(ra, plan, sms, st) : reach_dispatch(ra, plan, st, nullptr);
-    if (e != cudaSuccess) return cuda_fail(e);
+    // (the groups' launches share the run lists: they run one after another on the stream)
+    for (uint32_t g = 0; g < n_launch; ++g) {
+        e = lockstep ? piece_dispatch(ras[g], plans[g], sms, st) : reach_dispatch(ras[g], plans[g], st, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     if (spc > 1) {
         // compose each chunk's piece functions, kComposeGroup per thread and level, then apply
         // them to the interface slots' start states
-        const uint16_t *in = ra.maps;
+        const uint16_t *in = pmaps;
         uint64_t in_per = spc;
         uint16_t *bufs[2] = {reinterpret_cast<uint16_t *>(base + L.comp_off),
                              reinterpret_cast<uint16_t *>(base + L.comp_off + ((comp_funcs * NS * 2 + 255) & ~255ull))};
@@ -1501,7 +1530,7 @@ int launch_with_buffers(const HostAutomaton &H, const PreparedBuffers &B, const 
         1, (nbound + kJoinThreads * per_thread - 1) / (kJoinThreads * per_thread)));
     Automaton A{B.trans, B.classmap, B.final_bits, B.ifmask, B.slot_state,
                 H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
-    ReachArgs ra{A, d_text, len, n_chunks, B.maps, B.dinfo, B.status, 8, nullptr, nullptr};
+    ReachArgs ra{A, d_text, len, n_chunks, B.maps, B.dinfo, B.status, 8, nullptr, nullptr, H.k};
     ReachPlan plan;
     int err = plan_reach(A, nullptr, d_text, ra, sms, &plan);
     if (err != RIDFA_OK) return err;

@@ -62,6 +62,8 @@ struct ReachArgs {
     uint32_t probe;
     RunEntry *runs;           // [grid warps][kRunsPerWarp], or null: only single-run hand-offs
     uint32_t *finals;         // [grid warps][kFinalsPerWarp]
+    uint32_t stride;          // entries between consecutive rows of maps (A.k, or wider when the
+                              // slots are one group of a larger row)
 };
 
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {

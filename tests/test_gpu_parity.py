@@ -332,3 +332,26 @@ def test_compact_table_runs_finished_together():
         for c in (23, 100):
             for tuning in (None, dict(text_path=3), dict(text_path=5, block_threads=64)):
                 check(re_src, t, c, dfa_too=False, rows=list(range(c)), tuning=tuning)
+
+
+def test_pieces_in_state_groups():
+    """Automata of more than 256 states (regexp family k = 7: 273; codon RE {2,4}: 424; the
+    reading-frame RE: 825) run their pieces in groups of at most 256 states, one reach launch per
+    group into one row of all states; the composed rows equal the oracle's, pieces on (automatic
+    and forced) and off."""
+    rng = np.random.Generator(np.random.PCG64(104))
+    codons = [a + b + c for a in "ACGT" for b in "ACGT" for c in "ACGT"]
+    parts = []
+    while sum(map(len, parts)) < 120_000:
+        parts.append("".join(rng.choice(codons, int(rng.integers(0, 12)))) + "ATG" +
+                     "".join(rng.choice(codons, int(rng.integers(2, 7)))) + "TAG")
+    orf = np.frombuffer("".join(parts).encode(), dtype=np.uint8)
+    cases = [(textgen.regexp_family_re(7), textgen.regexp_family_text(100_000, 105), True),
+             (textgen.C2_RE.replace("{20,60}", "{2,4}"), textgen.c2_text(100_000, seed=106), False),
+             ("(([ACGT]{3})*ATG([ACGT]{3}){2,6}(TAA|TAG|TGA))*", orf, False),
+             ("(([ACGT]{3})*ATG([ACGT]{3}){2,6}(TAA|TAG|TGA))*", np.concatenate([orf[:777], orf[778:]]), False)]
+    for re_src, x, dfa_too in cases:
+        assert lib.ridfa_compile(re_src).info["n_states"] > 256
+        for c in (1, 3, 7):
+            for piece in (0, 1, 256):
+                check(re_src, x, c, dfa_too=dfa_too, rows=list(range(c)), tuning=dict(piece_len=piece))
