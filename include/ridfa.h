@@ -112,6 +112,10 @@ typedef struct {
                                  interleaved; 5 as 3, and a lane finishes all the runs its chunk
                                  handed off in one pass over the chunk (at most 512 threads a
                                  block).  2 to 5 need a 16-byte-aligned d_text (E_ARG otherwise) */
+    uint32_t lookback_cap;    /* pieces of automata with more than 256 states and k <= 32 start
+                                 from look-back start sets of at most this many states (0 = 32,
+                                 the largest; 1..32); a piece whose set stays larger has its whole
+                                 function computed from every state instead.  E_ARG above 32 */
 } ridfa_tuning;
 
 /* Compile `re` (re_len bytes, need not be NUL-terminated) on the host: position NFA, RI-DFA

@@ -42,7 +42,7 @@ class Info(_c.Structure):
 class Tuning(_c.Structure):
     _fields_ = [("piece_len", _u32), ("block_threads", _u32), ("probe_interval", _u32),
                 ("grid_blocks", _u32), ("profile", _u32), ("table_mode", _u32),
-                ("text_path", _u32)]
+                ("text_path", _u32), ("lookback_cap", _u32)]
 
 
 def _decl(name, res, args):
@@ -208,7 +208,8 @@ def _tuning(t):
         return _c.byref(t)
     return _c.byref(Tuning(t.get("piece_len", 0), t.get("block_threads", 0),
                            t.get("probe_interval", 0), t.get("grid_blocks", 0),
-                           t.get("profile", 0), t.get("table_mode", 0), t.get("text_path", 0)))
+                           t.get("profile", 0), t.get("table_mode", 0), t.get("text_path", 0),
+                           t.get("lookback_cap", 0)))
 
 
 def _recognize_sync(fn, name, prog, text, length, n_chunks, tuning, maps, stream):

@@ -107,7 +107,7 @@ int smem_optin_limit() {
 
 namespace {
 
-template <int R, class LUT, int BLOCK, int PATH>
+template <int R, class LUT, int BLOCK, int PATH, bool PSLOT = false>
 __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int table_in_smem,
                                                             uint32_t staging_offset) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -138,13 +138,14 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
     uint32_t *wball = wfin ? wfin + kRunsPerWarp : nullptr;
 
     // slot start states of this lane (slot a = r*32 + lane)
+    static_assert(!PSLOT || R == 1, "per-chunk start states take one register");
     uint32_t start_state[R];
     uint32_t start_live = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const uint32_t a = r * 32 + lane;
-        start_state[r] = a < A.k ? T.enc(A.slot_state[a]) : dead;
-        if (r * 32 < static_cast<int>(A.k)) start_live |= 1u << r;
+        start_state[r] = (!PSLOT && a < A.k) ? T.enc(A.slot_state[a]) : dead;
+        if (!PSLOT && r * 32 < static_cast<int>(A.k)) start_live |= 1u << r;
     }
 
     for (uint64_t task = warp0; task < n_tasks; task += n_warps) {
@@ -164,6 +165,12 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
             if (ch >= p.c) break;
             const uint64_t beg = chunk_begin(ch, p.len, p.c);
             const uint64_t end = chunk_begin(ch + 1, p.len, p.c);
+            if constexpr (PSLOT) {
+                // this chunk's own start states (one register: at most 32)
+                const uint32_t v = p.piece_slots[ch * 32 + lane];
+                start_state[0] = v < A.n ? T.enc(v) : dead;
+                start_live = __any_sync(kFull, start_state[0] != dead) ? 1u : 0u;
+            }
             uint32_t d, alive[R];
             uint64_t hp = 0;
             const int m = speculate<R, LUT>(T, A, p.text, beg, end, p.probe, lane, start_state, start_live, dead,
@@ -988,6 +995,132 @@ cudaError_t piece_r(int R, const ReachArgs &a, int grid, size_t smem, int tis, c
     }
 }
 
+// Look-back start sets for pieces (automata too large to run every piece from every state):
+// inside chunk i, the run's state at piece j's first byte b is delta(y, text[w, b)) for the state
+// y it had at w, for any w from the chunk start b_i to b, so it lies in delta(P, text[w, b)), the
+// states that survive the window from every state.  One warp per piece: for windows of 16, 64,
+// 256, ... bytes back (never before b_i) every state is run over the window, 32 at a time, and the
+// distinct live end states are gathered; once at most 32 remain they are the piece's start set.
+// The first piece of a chunk starts from the interface slots (k <= 32).  A piece whose set never
+// falls to 32 has its whole function written here instead: every state run over the piece.
+struct LookbackArgs {
+    Automaton A;              // A.slot_state[0..k): the interface slots' start states
+    const uint8_t *text;
+    uint64_t len;
+    uint64_t pieces;          // c * spc
+    uint32_t spc;             // pieces per chunk
+    uint16_t *slots;          // [pieces][32] start states, 0xFFFF = none
+    uint16_t *F;              // [pieces][A.n] piece functions, pre-filled with 0xFFFF
+    uint32_t cap;             // largest start set kept (1..32)
+};
+
+constexpr int kLbRegs = 4;         // states per lane and pass of the look-back kernel
+
+// Every state x in [s0, s0 + 32*kLbRegs) run over text[w, e) (the warp in lockstep, all lanes on
+// the same byte); the live end states, in the policy's encoding, in s[].
+template <class LUT>
+__device__ __forceinline__ void run_all_states(const LUT &T, const Automaton &A, const uint8_t *text, uint64_t w,
+                                               uint64_t e, uint32_t s0, uint32_t lane, uint32_t dead,
+                                               uint32_t (&s)[kLbRegs]) {
+#pragma unroll
+    for (int r = 0; r < kLbRegs; ++r) {
+        const uint32_t x = s0 + r * 32 + lane;
+        s[r] = x < A.n ? T.enc(x) : dead;
+    }
+    for (uint64_t q = w; q < e;) {
+        const uint64_t stop = min(e, q + 8);
+        for (; q < stop; ++q) {
+            const uint32_t c = T.cls_of(__ldg(text + q));
+#pragma unroll
+            for (int r = 0; r < kLbRegs; ++r) s[r] = T.next(s[r], c);
+        }
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < kLbRegs; ++r) any |= s[r] != dead;
+        if (!__any_sync(kFull, any)) break;
+    }
+}
+
+template <class LUT>
+__global__ void __launch_bounds__(512, 1) rid_lookback_kernel(LookbackArgs p, int table_in_smem) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const Automaton &A = p.A;
+    LUT T;
+    T.setup(A, smem, table_in_smem != 0);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t dead = T.enc(A.n);
+    const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t j = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < p.pieces; j += nw) {
+        uint16_t *out = p.slots + j * 32;
+        const uint64_t t = j % p.spc;
+        if (t == 0) {
+            out[lane] = lane < A.k ? A.slot_state[lane] : kUndef;
+            continue;
+        }
+        const uint64_t b = chunk_begin(j, p.len, p.pieces);
+        const uint64_t cb = chunk_begin(j - t, p.len, p.pieces);
+        uint32_t mine = kUndef;             // lane g: the g-th surviving state
+        bool found = false;
+        for (uint64_t L = 16;; L *= 4) {
+            const uint64_t w = b - cb <= L ? cb : b - L;
+            uint32_t cnt = 0;
+            mine = kUndef;
+            bool over = false;
+            for (uint32_t s0 = 0; s0 < A.n && !over; s0 += 32 * kLbRegs) {
+                uint32_t s[kLbRegs];
+                run_all_states(T, A, p.text, w, b, s0, lane, dead, s);
+#pragma unroll
+                for (int r = 0; r < kLbRegs; ++r) {
+                    uint32_t v = s[r] != dead ? T.id(s[r]) : kUndef;
+                    for (uint32_t g = 0; g < cnt; ++g)          // already gathered
+                        if (__shfl_sync(kFull, mine, g) == v) v = kUndef;
+                    while (!over) {                             // new ones, ascending
+                        const uint32_t lo = __reduce_min_sync(kFull, v);
+                        if (lo == kUndef) break;
+                        if (cnt == p.cap) {
+                            over = true;
+                            break;
+                        }
+                        if (lane == cnt) mine = lo;
+                        ++cnt;
+                        if (v == lo) v = kUndef;
+                    }
+                }
+            }
+            if (!over) {
+                found = true;
+                break;
+            }
+            if (w == cb) break;
+        }
+        out[lane] = static_cast<uint16_t>(found ? mine : kUndef);
+        if (!found) {
+            // no small start set: the piece's whole function, every state over the piece
+            const uint64_t e = chunk_begin(j + 1, p.len, p.pieces);
+            for (uint32_t s0 = 0; s0 < A.n; s0 += 32 * kLbRegs) {
+                uint32_t s[kLbRegs];
+                run_all_states(T, A, p.text, b, e, s0, lane, dead, s);
+#pragma unroll
+                for (int r = 0; r < kLbRegs; ++r) {
+                    const uint32_t x = s0 + r * 32 + lane;
+                    if (x < A.n) p.F[j * A.n + x] = s[r] != dead ? static_cast<uint16_t>(T.id(s[r])) : kUndef;
+                }
+            }
+        }
+    }
+}
+
+// Piece rows of the per-piece start sets (slot g of piece j started from slots[j][g]) scattered
+// into the piece functions: F_j(slots[j][g]) = row_j[g].  One thread per (piece, slot).
+__global__ void rid_scatter_kernel(const uint16_t *slots, const uint16_t *rows, uint64_t pieces, uint32_t P,
+                                   uint16_t *F) {
+    const uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= pieces * 32) return;
+    const uint32_t x = slots[t];
+    if (x < P) F[(t >> 5) * P + x] = rows[t];
+}
+
 // A chunk cut into pieces y_i = p_1 ... p_s: each piece is run from every state x of the automaton
 // (the reach kernel with every state as a slot), giving f_j(x) = δ(x, p_j) or ⊥, and
 // δ(x, y_i) = f_s(...f_1(x)) because the automaton is deterministic; the chunk's map row is that
@@ -1056,11 +1189,11 @@ __global__ void rid_apply_kernel(const uint16_t *F, uint32_t P, const uint16_t *
 
 struct Layout {   // scratch layout for one call
     size_t maps_off, dinfo_off, partials_off, ticket_off, status_off, accept_off, runs_off, finals_off,
-        summary_off, pmaps_off, pdinfo_off, comp_off, total;
+        summary_off, pmaps_off, pdinfo_off, comp_off, lbslots_off, lbrows_off, total;
 };
 
 Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks, uint64_t grid_warps,
-                  uint64_t pieces = 0, uint32_t P = 0, uint64_t comp_funcs = 0) {
+                  uint64_t pieces = 0, uint32_t P = 0, uint64_t comp_funcs = 0, bool lookback = false) {
     auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
     Layout L{};
     size_t off = 0;
@@ -1075,6 +1208,8 @@ Layout layout_for(uint64_t c, uint32_t k, bool need_maps, uint32_t join_blocks, 
     L.pmaps_off = off; off += al(pieces * P * 2);
     L.pdinfo_off = off; off += al(pieces * 4);
     L.comp_off = off; off += 2 * al(comp_funcs * P * 2);      // two buffers of composed functions
+    L.lbslots_off = off; off += lookback ? al(pieces * 32 * 2) : 0;   // look-back start sets
+    L.lbrows_off = off; off += lookback ? al(pieces * 32 * 2) : 0;    // their rows
     L.maps_off = off; off += need_maps ? al(c * k * 2) : 0;
     L.total = off;
     return L;
@@ -1122,6 +1257,7 @@ struct ReachPlan {
     int grid = 1;
     size_t smem = 0;
     uint32_t staging_offset = 0;
+    bool pslot = false;          // per-chunk start states (ReachArgs::piece_slots; R = 1 only)
 };
 
 template <int R, int PATH = kPathCoop>
@@ -1136,6 +1272,12 @@ cudaError_t reach_one(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, 
     using KernT = void (*)(ReachArgs, int, uint32_t);
     KernT kern = PATH == kPathCoop2 ? rid_reach2_kernel<R, LUT, block_cap2<R>()>
                                     : rid_reach_kernel<R, LUT, block_cap<R, PATH>(), PATH == kPathCoop2 ? kPathGlobal : PATH>;
+    if (pl.pslot) {
+        if constexpr (R == 1 && (PATH == kPathGlobal || PATH == kPathCoop || PATH == kPathCoopSet))
+            kern = rid_reach_kernel<1, LUT, block_cap<1, PATH>(), PATH, true>;
+        else
+            return cudaErrorInvalidValue;
+    }
     cudaError_t e = ensure_smem_cap(reinterpret_cast<const void *>(kern), pl.smem);
     if (e != cudaSuccess) return e;
     if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, pl.block, pl.smem);
@@ -1188,6 +1330,30 @@ cudaError_t piece_dispatch(const ReachArgs &a, const ReachPlan &pl, int sms, cud
         case kModePlain: return piece_r<LutPlain>(pl.R, a, grid, smem, pl.tis, st);
         default: return piece_r<LutFlat>(pl.R, a, grid, smem, pl.tis, st);
     }
+}
+
+// Launch the look-back kernel: its work is latency-bound lockstep runs, so it takes the compact
+// table (small, leaving room for many warps) whatever layout the reach launch uses.
+template <class LUT>
+cudaError_t lookback_one(const LookbackArgs &a, int sms, size_t smem, int tis, cudaStream_t st) {
+    auto kern = rid_lookback_kernel<LUT>;
+    cudaError_t e = ensure_smem_cap(reinterpret_cast<const void *>(kern), smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t blocks = (a.pieces + 15) / 16;
+    const int grid = static_cast<int>(std::min<uint64_t>(blocks, static_cast<uint64_t>(sms) * std::max(per_sm, 1)));
+    kern<<<grid, 512, smem, st>>>(a, tis);
+    return cudaGetLastError();
+}
+
+cudaError_t lookback_dispatch(const LookbackArgs &a, int sms, cudaStream_t st) {
+    const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024;
+    if (LutPlain::fits(a.A) && LutPlain::smem_bytes(a.A) <= limit)
+        return lookback_one<LutPlain>(a, sms, LutPlain::smem_bytes(a.A), 0, st);
+    const size_t flat = LutFlat::smem_bytes(a.A);
+    return flat <= limit ? lookback_one<LutFlat>(a, sms, flat, 1, st) : lookback_one<LutFlat>(a, sms, 256, 0, st);
 }
 
 // Choose the layout of a reach launch.  Defaults: the smallest lane-replicated table that fits
@@ -1344,21 +1510,29 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     const uint32_t piece_req = tuning ? tuning->piece_len : 0;
     if (piece_req > 1 && piece_req < 64) return RIDFA_E_ARG;
     const uint32_t NS = H.n_states;
-    const uint32_t groups = (NS + RIDFA_MAX_SLOTS - 1) / RIDFA_MAX_SLOTS;
+    // automata of more than 256 states whose interface fits one register start each piece from its
+    // look-back start set instead (one launch, no repeated runs)
+    const uint32_t text_path = tuning ? tuning->text_path : 0;
+    const bool lb_able = NS > RIDFA_MAX_SLOTS && H.k <= 32 && text_path != 2 && text_path != 4;
+    const uint32_t lb_cap = tuning && tuning->lookback_cap ? tuning->lookback_cap : 32;
+    if (lb_cap > 32) return RIDFA_E_ARG;
+    const uint32_t groups = lb_able ? 1 : (NS + RIDFA_MAX_SLOTS - 1) / RIDFA_MAX_SLOTS;
     uint64_t spc = 1;                                  // pieces per chunk
     if (piece_req != 1 && NS >= 1 && groups <= kMaxPieceGroups) {
         const uint64_t warps = static_cast<uint64_t>(sms) * 32, lanes = warps * 32;
         const uint64_t rall = NS <= 32 ? 1 : NS <= 64 ? 2 : NS <= 128 ? 4 : 8;
         // a short text: a lockstep piece costs a warp (1 + ceil(P/32)) lookups per byte where a
         // chunk costs a lane 2, worth it only while the chunks leave most resident warps idle
-        if (groups == 1 && c * (1 + rall) * 4 <= warps) {
+        if (NS <= RIDFA_MAX_SLOTS && c * (1 + rall) * 4 <= warps) {
             const uint64_t plen = piece_req >= 64 ? piece_req : 256;
             spc = std::min<uint64_t>(2 * lanes / c, len / (c * plen));
         }
-        // a long text in chunks that fill at most half of the lanes (a quarter per state group when
-        // the states run in groups, whose launches repeat the merged runs): pieces through the
-        // reach kernel, at most one per lane, at least kManyPieceLen bytes each
-        if (spc < 2 && c * (groups == 1 ? 2 : 4 * groups) <= lanes) {
+        // a long text in chunks that fill at most half of the lanes (a quarter with look-back start
+        // sets, whose look-back costs extra; a quarter per state group when the states run in
+        // groups, whose launches repeat the merged runs): pieces through the reach kernel, at most
+        // one per lane, at least kManyPieceLen bytes each
+        const uint64_t fill = lb_able ? 4 : groups == 1 ? 2 : 4 * groups;
+        if (spc < 2 && c * fill <= lanes) {
             const uint64_t plen = piece_req >= 64 ? piece_req : kManyPieceLen;
             spc = std::min<uint64_t>(lanes / c, len / (c * plen));
         }
@@ -1366,24 +1540,27 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     }
     // many pieces (a long text in few chunks): the reach kernel runs them, one lane per piece
     // once its runs merge; few pieces: one lockstep warp per piece
-    const bool lockstep = spc > 1 && groups == 1 && c * spc <= static_cast<uint64_t>(sms) * 32 * 8;
+    const bool lockstep = spc > 1 && NS <= RIDFA_MAX_SLOTS && c * spc <= static_cast<uint64_t>(sms) * 32 * 8;
     const uint64_t pieces = c * spc;
+    const bool lookback = spc > 1 && lb_able;
     const uint32_t n_launch = spc > 1 ? groups : 1;
     // plan the reach launches first: the run-list scratch is sized by their grids
     ReachArgs ras[kMaxPieceGroups];
     ReachPlan plans[kMaxPieceGroups];
     uint64_t grid_warps = 0;
     for (uint32_t g = 0; g < n_launch; ++g) {
-        const uint32_t kg = spc > 1 ? std::min<uint32_t>(RIDFA_MAX_SLOTS, NS - g * RIDFA_MAX_SLOTS) : H.k;
+        // look-back pieces: 32 start slots per piece, rows of 32 scattered afterwards
+        const uint32_t kg = lookback ? 32 : spc > 1 ? std::min<uint32_t>(RIDFA_MAX_SLOTS, NS - g * RIDFA_MAX_SLOTS) : H.k;
         const Automaton Ag = spc > 1 ? Automaton{D->trans, D->classmap, D->final_bits, D->ifmask,
-                                                 D->all_states + g * RIDFA_MAX_SLOTS, H.n_states, H.n_classes,
-                                                 kg, (kg + 31) / 32, 0}
+                                                 lookback ? D->slot_state : D->all_states + g * RIDFA_MAX_SLOTS,
+                                                 H.n_states, H.n_classes, kg, (kg + 31) / 32, 0}
                                      : A;
         ras[g] = ReachArgs{Ag, d_text, len, static_cast<uint32_t>(pieces), nullptr, nullptr, nullptr, 8,
-                           nullptr, nullptr, spc > 1 ? NS : H.k};
+                           nullptr, nullptr, lookback ? 32u : spc > 1 ? NS : H.k, nullptr};
         if (tuning && tuning->probe_interval) ras[g].probe = tuning->probe_interval;
         err = plan_reach(ras[g].A, tuning, d_text, ras[g], sms, &plans[g]);
         if (err != RIDFA_OK) return err;
+        plans[g].pslot = lookback;
         // warps past the last 32-chunk task never write their run list (the lockstep kernel has none)
         if (!lockstep)
             grid_warps = std::max<uint64_t>(grid_warps, std::min<uint64_t>(static_cast<uint64_t>(plans[g].grid) *
@@ -1392,7 +1569,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     }
     const uint64_t comp_funcs = spc > 1 ? c * ((spc + kComposeGroup - 1) / kComposeGroup) : 0;
     const Layout L = layout_for(c, H.k, d_maps_user == nullptr, join_blocks, grid_warps, spc > 1 ? pieces : 0,
-                                spc > 1 ? NS : 0, comp_funcs);
+                                spc > 1 ? NS : 0, comp_funcs, lookback);
     DeviceScratch *S = scratch_for(P, dev, L.total, &err);
     if (!S) return err;
     uint8_t *base = static_cast<uint8_t *>(S->base);
@@ -1406,7 +1583,9 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     uint16_t *pmaps = reinterpret_cast<uint16_t *>(base + L.pmaps_off);
     for (uint32_t g = 0; g < n_launch; ++g) {
         ReachArgs &ra = ras[g];
-        ra.maps = spc > 1 ? pmaps + g * RIDFA_MAX_SLOTS : maps;
+        ra.maps = lookback ? reinterpret_cast<uint16_t *>(base + L.lbrows_off)
+                  : spc > 1 ? pmaps + g * RIDFA_MAX_SLOTS : maps;
+        if (lookback) ra.piece_slots = reinterpret_cast<const uint16_t *>(base + L.lbslots_off);
         ra.dinfo = spc > 1 ? reinterpret_cast<uint32_t *>(base + L.pdinfo_off) : dinfo;
         ra.status = spc > 1 ? piece_status : status;
         ra.runs = reinterpret_cast<RunEntry *>(base + L.runs_off);
@@ -1426,9 +1605,27 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
             }
         cudaEventRecord(static_cast<cudaEvent_t>(S->ev[0]), st);
     }
+    if (lookback) {
+        // piece functions start undefined; the look-back kernel writes each piece's start set (or
+        // the whole function of a piece without a small one)
+        e = cudaMemsetAsync(pmaps, 0xFF, pieces * NS * 2, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        LookbackArgs la{ras[0].A, d_text, len, pieces, static_cast<uint32_t>(spc),
+                        reinterpret_cast<uint16_t *>(base + L.lbslots_off), pmaps, lb_cap};
+        la.A.k = H.k;
+        e = lookback_dispatch(la, sms, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     // (the groups' launches share the run lists: they run one after another on the stream)
     for (uint32_t g = 0; g < n_launch; ++g) {
         e = lockstep ? piece_dispatch(ras[g], plans[g], sms, st) : reach_dispatch(ras[g], plans[g], st, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (lookback) {
+        rid_scatter_kernel<<<static_cast<unsigned>((pieces * 32 + 255) / 256), 256, 0, st>>>(
+            reinterpret_cast<const uint16_t *>(base + L.lbslots_off),
+            reinterpret_cast<const uint16_t *>(base + L.lbrows_off), pieces, NS, pmaps);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e);
     }
     if (spc > 1) {

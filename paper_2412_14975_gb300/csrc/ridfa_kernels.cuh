@@ -64,6 +64,8 @@ struct ReachArgs {
     uint32_t *finals;         // [grid warps][kFinalsPerWarp]
     uint32_t stride;          // entries between consecutive rows of maps (A.k, or wider when the
                               // slots are one group of a larger row)
+    const uint16_t *piece_slots;   // [c][32] per-chunk start states (0xFFFF: none), or null: the
+                                   // slots' start states A.slot_state for every chunk
 };
 
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {

@@ -334,11 +334,14 @@ def test_compact_table_runs_finished_together():
                 check(re_src, t, c, dfa_too=False, rows=list(range(c)), tuning=tuning)
 
 
-def test_pieces_in_state_groups():
-    """Automata of more than 256 states (regexp family k = 7: 273; codon RE {2,4}: 424; the
-    reading-frame RE: 825) run their pieces in groups of at most 256 states, one reach launch per
-    group into one row of all states; the composed rows equal the oracle's, pieces on (automatic
-    and forced) and off."""
+def test_pieces_large_automata():
+    """Automata of more than 256 states.  With k <= 32 (regexp family k = 7: 273 states; codon RE
+    {2,4}: 424; the reading-frame RE: 825) each piece starts from its look-back start set (the
+    chunk's first piece from the interface slots) and the rows are scattered into the piece
+    functions; with the start sets capped below their size the pieces fall back to whole functions
+    from every state.  With k > 32 (a prefixed regexp family: 303 states, k = 38) the pieces run
+    from every state in groups of at most 256, one reach launch per group.  The composed rows equal
+    the oracle's, pieces on (automatic and forced) and off."""
     rng = np.random.Generator(np.random.PCG64(104))
     codons = [a + b + c for a in "ACGT" for b in "ACGT" for c in "ACGT"]
     parts = []
@@ -350,8 +353,22 @@ def test_pieces_in_state_groups():
              (textgen.C2_RE.replace("{20,60}", "{2,4}"), textgen.c2_text(100_000, seed=106), False),
              ("(([ACGT]{3})*ATG([ACGT]{3}){2,6}(TAA|TAG|TGA))*", orf, False),
              ("(([ACGT]{3})*ATG([ACGT]{3}){2,6}(TAA|TAG|TGA))*", np.concatenate([orf[:777], orf[778:]]), False)]
+    pre = "ghijklmnopqrstuvwxyzGHIJKLMNOP"
+    words = []
+    while sum(map(len, words)) < 100_000:
+        ab = "".join(rng.choice(["a", "b"], int(rng.integers(8, 300))))
+        words.append(pre + ab[:-8] + "a" + ab[-7:])
+    cases.append(("(" + pre + "(a|b)*a(a|b){7})*", np.frombuffer("".join(words).encode(), dtype=np.uint8), False))
     for re_src, x, dfa_too in cases:
-        assert lib.ridfa_compile(re_src).info["n_states"] > 256
+        info = lib.ridfa_compile(re_src).info
+        assert info["n_states"] > 256
         for c in (1, 3, 7):
             for piece in (0, 1, 256):
                 check(re_src, x, c, dfa_too=dfa_too, rows=list(range(c)), tuning=dict(piece_len=piece))
+        if info["k"] <= 32:
+            for cap in (1, 3):
+                check(re_src, x, 3, dfa_too=False, rows=[0, 1, 2], tuning=dict(piece_len=256, lookback_cap=cap))
+    prog = lib.ridfa_compile(cases[0][0])
+    with pytest.raises(lib.RidfaError) as e:
+        lib.ridfa_recognize(prog, to_device(cases[0][1]), cases[0][1].size, 3, tuning=dict(lookback_cap=33))
+    assert e.value.code == -1
