@@ -1128,6 +1128,7 @@ __global__ void rid_scatter_kernel(const uint16_t *slots, const uint16_t *rows, 
 constexpr uint32_t kComposeGroup = 32;     // functions composed per thread and level
 constexpr uint32_t kMaxPieceGroups = 4;    // pieces for automata of up to 4 x 256 states
 constexpr uint64_t kManyPieceLen = 1024;   // shortest piece of the many-pieces path (bytes)
+constexpr uint64_t kMaxPieceBytes = 1ull << 30;   // scratch of the piece functions, at most
 
 // One level: function g of chunk i = the composition, in order, of input functions
 // [g*G, (g+1)*G) of that chunk.  One thread per (chunk, group, start state).
@@ -1536,6 +1537,8 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
             const uint64_t plen = piece_req >= 64 ? piece_req : kManyPieceLen;
             spc = std::min<uint64_t>(lanes / c, len / (c * plen));
         }
+        // the piece functions take pieces * P * 2 bytes of scratch: at most kMaxPieceBytes
+        spc = std::min<uint64_t>(spc, kMaxPieceBytes / (c * NS * 2));
         if (spc < 2) spc = 1;
     }
     // many pieces (a long text in few chunks): the reach kernel runs them, one lane per piece

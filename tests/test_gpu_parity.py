@@ -372,3 +372,35 @@ def test_pieces_large_automata():
     with pytest.raises(lib.RidfaError) as e:
         lib.ridfa_recognize(prog, to_device(cases[0][1]), cases[0][1].size, 3, tuning=dict(lookback_cap=33))
     assert e.value.code == -1
+
+
+def test_lookback_pieces_unaligned_and_accept_only():
+    """Look-back pieces on a text that starts off a 16-byte boundary (plain global loads), with
+    and without chunk maps requested (accept only: the library's own scratch), and on a mutated
+    text whose reading frame breaks in a middle piece."""
+    re_src = "(([ACGT]{3})*ATG([ACGT]{3}){2,6}(TAA|TAG|TGA))*"
+    o, ser = oracle(re_src)
+    prog = lib.ridfa_compile(re_src)
+    rng = np.random.Generator(np.random.PCG64(107))
+    codons = [a + b + c for a in "ACGT" for b in "ACGT" for c in "ACGT"]
+    parts = []
+    while sum(map(len, parts)) < 150_000:
+        parts.append("".join(rng.choice(codons, int(rng.integers(0, 12)))) + "ATG" +
+                     "".join(rng.choice(codons, int(rng.integers(2, 7)))) + "TAA")
+    x = np.frombuffer("".join(parts).encode(), dtype=np.uint8)
+    y = np.concatenate([x[:70_001], x[70_002:]])
+    for t in (x, y):
+        want_acc = ser.accepts(t)
+        base = torch.from_numpy(np.concatenate([np.zeros(16, np.uint8), t])).to("cuda:0")
+        for off in (0, 3):
+            d = base[16 - off:] if off else base[16:]
+            src = np.concatenate([np.zeros(off, np.uint8), t]) if off else t
+            n = src.size
+            for c in (2, 5):
+                acc, maps = run(lib, prog, d, n, c, tuning=dict(piece_len=512))
+                assert acc == ser.accepts(src)
+                want = o.lambda_rows(src, c, range(c))
+                for i in range(c):
+                    assert np.array_equal(maps[i], want[i]), (off, c, i)
+                assert lib.ridfa_recognize(prog, d, n, c, tuning=dict(piece_len=512)) == ser.accepts(src)
+        assert lib.ridfa_recognize(prog, base[16:], t.size, 4) == want_acc
