@@ -165,7 +165,7 @@ def cpu_baseline(name, re_src, budget_s=12.0, seed=7):
     ser.accepts(x)
     dt = time.perf_counter() - t
     rate = x.size / max(dt, 1e-9)
-    n2 = int(min(256 << 20, max(n, rate * budget_s)))
+    n2 = int(min(2 << 30, max(n, rate * budget_s)))
     if n2 > x.size:
         x = sample_text_numpy(name, n2, seed + 1)
         t = time.perf_counter()
