@@ -1369,9 +1369,9 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     uint32_t mode = tuning ? tuning->table_mode : 0;
     const size_t rep16 = LutRep<true>::smem_bytes(A), rep32 = LutRep<false>::smem_bytes(A),
                  part16 = LutPart::smem_bytes(A);
-    // (the half-replicated layout is only taken on request: on the codon RE, the one workload it
-    // would serve, it measured slower than the compact table -- its gathers conflict less, but
-    // its larger footprint leaves fewer warps and the time goes to run imbalance, not conflicts)
+    // (the half-replicated layout does not replace the compact one: on the codon RE it measured
+    // slower -- its gathers conflict less, but its larger footprint leaves fewer warps and the
+    // time goes to run imbalance, not conflicts)
     const size_t plain = LutPlain::smem_bytes(A), flat = LutFlat::smem_bytes(A), rep16x4 = LutRep16x4::smem_bytes(A);
     const bool ok16 = LutRep<true>::fits16(A) && rep16 <= limit, ok32 = rep32 <= limit,
                okp = LutPart::fits(A) && part16 <= limit, okplain = LutPlain::fits(A) && plain <= limit,
@@ -1381,8 +1381,23 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // table ran at a third of the speed of a 26-warp scaled one)
     const size_t room16w = 16 * static_cast<size_t>(kWarpCoopBytes);
     const bool roomy32 = ok32 && rep32 + room16w <= limit, roomy16x4 = ok16x4 && rep16x4 + room16w <= limit;
-    if (mode == 0)
+    if (mode == 0) {
         mode = ok16 ? kModeRep16 : roomy32 ? kModeRep32 : roomy16x4 ? kModeRep16x4 : ok32 ? kModeRep32 : kModePlain;
+        // a large conflict-free table gives way to the half-replicated one (at most two wavefronts
+        // a gather) when that leaves at least a quarter more warps: measured on the any-field
+        // record lines (Rep16x4, 23 warps: 2,330 GB/s; half-replicated, 31 warps: 2,548) and the
+        // regexp family (Rep32, 21 warps: 1,740; half-replicated: 2,080)
+        if ((mode == kModeRep32 || mode == kModeRep16x4) && okp) {
+            const size_t wmax = pl.R <= 4 ? 32 : 16;    // the block's warp cap
+            auto warps_beside = [&](size_t table) {
+                const size_t off = (table + 127) & ~static_cast<size_t>(127);
+                return std::min<size_t>(wmax, off < limit ? (limit - off) / kWarpCoopBytes : 0);
+            };
+            const size_t w_cf = warps_beside(mode == kModeRep32 ? rep32 : rep16x4);
+            const size_t w_part = warps_beside(part16);
+            if (4 * w_part >= 5 * w_cf) mode = kModePart16;
+        }
+    }
     if (mode == kModeRep16x4 && !ok16x4) return RIDFA_E_ARG;
     if (mode == kModePlain && !okplain) mode = kModeFlat;    // the compact table, through generic loads
     if ((mode == kModeRep16 && !ok16) || (mode == kModeRep32 && !ok32) || (mode == kModePart16 && !okp))
