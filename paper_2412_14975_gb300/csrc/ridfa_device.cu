@@ -9,10 +9,14 @@
 //     a = r*32 + lane in register r), all reading the same byte.  Every `probe` bytes the warp
 //     checks whether all live runs are in one state (redux min == max); runs that merged
 //     collapse into one (convergence), dead runs are dropped.
-//   * Converged phase: each lane takes its own chunk and finishes the single surviving run
-//     alone, with 16-byte vector loads of the text; the chunk map row is the surviving state
-//     for the slots alive at convergence and undefined for the others.
+//   * Converged phase: each lane takes its own chunk and finishes the surviving run alone (or,
+//     when the live runs sit in at most 8 distinct states, each of them as a run of its own, or
+//     all of them together on the set path), reading the text staged in shared memory or with
+//     16-byte vector loads; the chunk map row is the surviving state for the slots alive at
+//     convergence and undefined for the others.
 //   A chunk whose runs never merge finishes in the speculative phase.
+// Few chunks: each chunk is cut into pieces run from every state (or, for large automata, from
+// each piece's look-back start set) and the piece functions are composed into the chunk's row.
 // Join phase (Sec. 3.2 / 3.4): let D_i be the distinct defined values of lambda_i (m_i <= 32).
 // Between chunks i-1 and i the transfer is the m_{i-1} x m_i Boolean matrix
 //   M_i[x][y] = exists a in if_min({D_{i-1}[x]}) with lambda_i(a) = D_i[y],
