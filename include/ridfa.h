@@ -222,6 +222,14 @@ int ridfa_recognize(const ridfa_program *prog, const uint8_t *d_text, size_t len
                     uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *h_accept,
                     uint16_t *d_chunk_maps, void *stream);
 
+/* Failure detection of the device waits: the bounded mbarrier wait the bulk-copy text path uses
+ * (at most a fixed number of polls, then E_TIMEOUT with the context intact), exercised alone on
+ * `stream`.  One warp waits for the first phase of a fresh mbarrier, at most `limit` polls; with
+ * arrive != 0 the phase is completed first (returns RIDFA_OK), with arrive == 0 nothing arrives and
+ * the call returns RIDFA_E_TIMEOUT.  Allocates 4 device bytes; synchronises `stream`.
+ * Errors: E_NOMEM, E_CUDA. */
+int ridfa_check_bounded_wait(uint32_t limit, int arrive, void *stream);
+
 /* Recognize one text held in host memory: the len bytes at h_text are copied to the caller's
  * device buffer d_staging (at least len bytes; 16-byte aligned for the staged text paths) on
  * `stream`, then recognized as by ridfa_recognize; the accept bit comes back in *h_accept.

@@ -63,6 +63,7 @@ for _n in ("ridfa_recognize", "ridfa_recognize_async", "ridfa_recognize_dfa", "r
     _decl(_n, _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _c.POINTER(Tuning), _vp, _vp, _vp])
 _decl("ridfa_recognize_host", _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _c.POINTER(Tuning), _vp, _vp, _vp])
 _decl("ridfa_last_status", _c.c_int, [_vp, _vp])
+_decl("ridfa_check_bounded_wait", _c.c_int, [_u32, _c.c_int, _vp])
 _decl("ridfa_recognize_noalloc", _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _vp, _vp, _vp])
 _decl("ridfa_bench_smem_gather", _c.c_int, [_u32, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)])
 _decl("ridfa_bench_hbm_read", _c.c_int, [_vp, _c.c_size_t, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)])
@@ -241,6 +242,12 @@ def ridfa_recognize_host(prog, h_text, length, n_chunks, d_staging, tuning=None,
                                      _ptr(d_staging), _c.addressof(acc), _stream(stream)),
            "ridfa_recognize_host")
     return bool(acc.value)
+
+
+def ridfa_check_bounded_wait(limit, arrive, stream=None):
+    """Status code of one bounded device wait: RIDFA_OK (0) when the phase completed, -7
+    (E_TIMEOUT) when `limit` polls ran out (arrive=False: nothing ever arrives)."""
+    return int(_lib.ridfa_check_bounded_wait(int(limit), 1 if arrive else 0, _stream(stream)))
 
 
 def ridfa_recognize_async(prog, d_text, length, n_chunks, d_accept, tuning=None,

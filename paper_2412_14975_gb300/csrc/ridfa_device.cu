@@ -284,12 +284,9 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
                     auto wait_stage = [&]() -> bool {
                         const uint32_t bar = bar_base + (rctr % kStages) * 8;
                         const uint32_t parity = (rctr / kStages) & 1;
-                        for (uint32_t it = 0; it < kSpinLimit; ++it)
-                            if (__all_sync(kFull, mbar_try_wait(bar, parity))) {
-                                ++rctr;
-                                return true;
-                            }
-                        return false;
+                        if (!mbar_wait_warp(bar, parity, kSpinLimit)) return false;
+                        ++rctr;
+                        return true;
                     };
                     for (uint32_t i = 0; i < kStages; ++i) issue();
                     for (;;) {
@@ -328,8 +325,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
                         while (rctr < wctr) {
                             const uint32_t bar = bar_base + (rctr % kStages) * 8;
                             const uint32_t parity = (rctr / kStages) & 1;
-                            for (uint32_t it = 0; it < kSpinLimit && !__all_sync(kFull, mbar_try_wait(bar, parity)); ++it) {
-                            }
+                            (void)mbar_wait_warp(bar, parity, kSpinLimit);
                             ++rctr;
                         }
                         return;
@@ -1763,6 +1759,43 @@ int launch_with_buffers(const HostAutomaton &H, const PreparedBuffers &B, const 
 }
 
 }  // namespace ridfa
+
+namespace ridfa {
+namespace {
+// The bounded wait of the bulk-copy path, exercised alone: one warp waits on a fresh mbarrier for
+// its first phase, at most `limit` polls.  With `arrive` lane 0 completes the phase first; without
+// it nothing ever arrives and the wait must run out.  *status gets kStatusTimeout when it did.
+__global__ void rid_wait_check_kernel(uint32_t limit, int arrive, uint32_t *status) {
+    __shared__ __align__(8) uint64_t bar_word;
+    const uint32_t bar = smem_addr(&bar_word);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    fence_mbar_init();
+    __syncwarp();
+    if (arrive && threadIdx.x == 0) mbar_arrive(bar);
+    __syncwarp();
+    const bool ok = mbar_wait_warp(bar, 0, limit);
+    if (threadIdx.x == 0) *status = ok ? 0u : kStatusTimeout;
+}
+}  // namespace
+}  // namespace ridfa
+
+extern "C" int ridfa_check_bounded_wait(uint32_t limit, int arrive, void *stream) {
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t *d_status = nullptr;
+    cudaError_t e = cudaMalloc(&d_status, sizeof(uint32_t));
+    if (e != cudaSuccess) return ridfa::cuda_fail(e);
+    uint32_t h_status = 0;
+    e = cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) {
+        ridfa::rid_wait_check_kernel<<<1, 32, 0, st>>>(limit, arrive, d_status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_status);
+    if (e != cudaSuccess) return ridfa::cuda_fail(e);
+    return (h_status & ridfa::kStatusTimeout) ? RIDFA_E_TIMEOUT : RIDFA_OK;
+}
 
 extern "C" int ridfa_recognize(const ridfa_program *prog, const uint8_t *d_text, size_t len,
                                uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *h_accept,

@@ -104,3 +104,41 @@ def test_gloo_ranks_exchange_summaries(world):
             p.join(timeout=60)
             assert p.exitcode == 0
         assert sorted(res) == [(r, True) for r in range(world)]
+
+
+def _rank_dies_main(rank, world, port, out_q):
+    import datetime
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)                               # this rank dies before the exchange
+    buf = torch.zeros(16, dtype=torch.uint8)
+    try:
+        dist.all_gather([torch.empty_like(buf) for _ in range(world)], buf)
+        out_q.put((rank, "completed"))
+    except Exception as e:                        # the survivor learns of it from the collective
+        out_q.put((rank, "error:" + type(e).__name__))
+
+
+def test_gloo_rank_that_dies_fails_the_exchange():
+    """A shard rank that dies before the summary exchange makes the survivor's all-gather fail with
+    an error (closed connection or the short process-group timeout) instead of hanging."""
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_dies_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    rank, what = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and what.startswith("error:"), what
+    assert procs[1].exitcode == 3
