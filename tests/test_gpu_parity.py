@@ -280,7 +280,8 @@ def test_unminimized_interface_maps():
 
 
 def test_c3_64mib_sampled_rows():
-    """A larger record-line text in the bench's launch shape (many chunks), sampled rows."""
+    """A larger record-line text in 16,384 chunks (cut into pieces: the chunks fill under half of
+    the lanes), sampled rows."""
     x = textgen.c3_text(64 << 20, seed=0x5EED03)
     c = 1 << 14
     rows = sorted({0, 1, 2, c // 2, c - 2, c - 1} | set(
@@ -404,3 +405,33 @@ def test_lookback_pieces_unaligned_and_accept_only():
                     assert np.array_equal(maps[i], want[i]), (off, c, i)
                 assert lib.ridfa_recognize(prog, d, n, c, tuning=dict(piece_len=512)) == ser.accepts(src)
         assert lib.ridfa_recognize(prog, base[16:], t.size, 4) == want_acc
+
+
+def test_c3_4gib_bench_workload_sampled_rows():
+    """The bench's workload in its launch shape: 4 GiB of record lines generated on the device
+    with the bench's seed, 155,648 chunks.  Sampled rows equal the oracle's, chunk by chunk; the
+    accept bit equals the all-states DFA comparator's, and one byte outside the alphabet anywhere
+    makes both reject (properties that hold at any size)."""
+    import bench
+    from oracle.ridfa_sets import chunk_boundaries
+    d = bench.make_text("c3", 4 << 30, 0x5EED02, "cuda:0")
+    n, c = d.numel(), 155_648
+    o, _ = oracle(textgen.C3_RE)
+    prog = lib.ridfa_compile(textgen.C3_RE)
+    maps = torch.empty((c, prog.info["k"]), dtype=torch.int16, device="cuda:0")
+    acc = lib.ridfa_recognize(prog, d, n, c, d_chunk_maps=maps)
+    assert acc == lib.ridfa_recognize_dfa(prog, d, n, c) is True
+    b = chunk_boundaries(n, c)
+    rows = sorted({0, 1, c // 2, c - 2, c - 1} | set(np.random.Generator(np.random.PCG64(3)).integers(0, c, 12).tolist()))
+    got = maps[rows].cpu().numpy().view(np.uint16)
+    for g, i in zip(got, rows):
+        want = o.lambda_row(d[b[i]:b[i + 1]].cpu().numpy())
+        assert np.array_equal(g, want), i
+    pos = int(b[c // 3] + 1234)
+    keep = d[pos].item()
+    d[pos] = 0
+    assert lib.ridfa_recognize(prog, d, n, c) is False
+    assert lib.ridfa_recognize_dfa(prog, d, n, c) is False
+    d[pos] = keep
+    del d, maps
+    torch.cuda.empty_cache()
