@@ -106,12 +106,12 @@ typedef struct {
                                  4x larger than mode 2 allows) (E_ARG if the chosen layout does not
                                  fit) */
     uint32_t text_path;       /* how the converged runs read the text: 0 auto; 1 each lane's own
-                                 16-byte global loads; 2 per-lane bulk copies (cp.async.bulk)
-                                 into a shared-memory ring; 3 warp-cooperative coalesced loads
-                                 staged in shared memory; 4 the same with two chunks per lane,
-                                 interleaved; 5 as 3, and a lane finishes all the runs its chunk
-                                 handed off in one pass over the chunk (at most 512 threads a
-                                 block).  2 to 5 need a 16-byte-aligned d_text (E_ARG otherwise) */
+                                 16-byte global loads; 2 retired (per-lane bulk copies; E_ARG);
+                                 3 warp-cooperative coalesced loads staged in shared memory; 4
+                                 the same with two chunks per lane, interleaved; 5 as 3, and a
+                                 lane finishes all the runs its chunk handed off in one pass over
+                                 the chunk (at most 512 threads a block).  3 to 5 need a
+                                 16-byte-aligned d_text (E_ARG otherwise) */
     uint32_t lookback_cap;    /* pieces of automata with more than 256 states and k <= 32 start
                                  from look-back start sets of at most this many states (0 = 32,
                                  the largest; 1..32); a piece whose set stays larger has its whole
@@ -222,9 +222,10 @@ int ridfa_recognize(const ridfa_program *prog, const uint8_t *d_text, size_t len
                     uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *h_accept,
                     uint16_t *d_chunk_maps, void *stream);
 
-/* Failure detection of the device waits: the bounded mbarrier wait the bulk-copy text path uses
- * (at most a fixed number of polls, then E_TIMEOUT with the context intact), exercised alone on
- * `stream`.  One warp waits for the first phase of a fresh mbarrier, at most `limit` polls; with
+/* Failure detection of device waits: the library's bounded mbarrier wait (at most a fixed number
+ * of polls, then E_TIMEOUT with the context intact; the form any spin on a flag or barrier in
+ * these kernels must take -- the recognize kernels themselves currently have none, their tickets
+ * being atomics), exercised alone on `stream`.  One warp waits for the first phase of a fresh mbarrier, at most `limit` polls; with
  * arrive != 0 the phase is completed first (returns RIDFA_OK), with arrive == 0 nothing arrives and
  * the call returns RIDFA_E_TIMEOUT.  Allocates 4 device bytes; synchronises `stream`.
  * Errors: E_NOMEM, E_CUDA. */
@@ -274,7 +275,10 @@ int ridfa_recognize_dfa_async(const ridfa_program *prog, const uint8_t *d_text, 
  * Limits: the tables plus 4 bytes per chunk plus about 133 KiB of join scratch must fit in the
  * array, otherwise RIDFA_E_TOO_LARGE and nothing is launched.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call copies the program's tables into
+ * make that first call before any stream capture.  The address is kept for the life of the
+ * process, so the library must not be used across a cudaDeviceReset of that device.  The
+ * device status word (the join's consistency check, E_STATE on ridfa_recognize) is not reported
+ * by this call, which returns once its work is queued.  Every call copies the program's tables into
  * the array and clears the counters the join needs; the array keeps the last call's contents.
  * Calls that overlap on the GPU (on different streams, from different threads or programs) use
  * the same array and race: serialise them.

@@ -113,11 +113,6 @@ def _stream(s):
     return s.cuda_stream
 
 
-def chunk_boundaries(n, c):
-    """b_i = floor(i*n/c), i = 0..c (the chunking every entry point uses)."""
-    return [(i * n) // c for i in range(c + 1)]
-
-
 class Program:
     """Owns one ridfa_program*; freed with ridfa_free when collected or closed."""
 

@@ -983,6 +983,7 @@ extern "C" int ridfa_batch_create(const ridfa_program *const *progs, uint32_t n_
         if (it.prog >= n_progs || (it.len && !it.d_text)) return RIDFA_E_ARG;
         if (it.n_chunks > it.len || (it.len == 0 && it.n_chunks)) return RIDFA_E_CHUNKS;
     }
+    ridfa::NvtxRange range("ridfa batch create");
     ridfa_batch *B = new (std::nothrow) ridfa_batch();
     if (!B) return RIDFA_E_NOMEM;
     if (cudaGetDevice(&B->device) != cudaSuccess) {
@@ -1011,6 +1012,7 @@ extern "C" int ridfa_batch_create(const ridfa_program *const *progs, uint32_t n_
 
 extern "C" int ridfa_batch_run(ridfa_batch *b, void *stream) {
     if (!b) return RIDFA_E_ARG;
+    ridfa::NvtxRange range("ridfa batch run");
     return ridfa::batch_run(b, static_cast<cudaStream_t>(stream));
 }
 

@@ -689,6 +689,7 @@ bool build_min_dfa(const ClassNfa &N, uint32_t cap, ridfa_program &P) {
 extern "C" int ridfa_compile(const char *re, size_t re_len, const ridfa_compile_opts *opts,
                              ridfa_program **out) {
     if (!out || (!re && re_len)) return RIDFA_E_ARG;
+    ridfa::NvtxRange range("ridfa compile");
     ridfa_compile_opts o{1, 1, RIDFA_MAX_STATES};
     if (opts) o = *opts;
     uint32_t cap = (o.max_states == 0 || o.max_states > RIDFA_MAX_STATES) ? RIDFA_MAX_STATES : o.max_states;

@@ -118,19 +118,10 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
     const Automaton &A = p.A;
     LUT T;
     T.setup(A, smem, table_in_smem != 0);
-    // per-warp staging ring and its mbarriers (bulk-copy path only)
+    // per-warp staging buffers of the cooperative text paths
     const uint32_t warp_in_block = threadIdx.x >> 5;
-    const uint32_t stg_base = smem_addr(smem) + staging_offset +
-                              warp_in_block * (PATH == kPathCoop || PATH == kPathCoopSet ? kWarpCoopBytes : kWarpStageBytes);
-    const uint32_t bar_base = stg_base + kStages * 32 * kLaneStride;
-    if (PATH == kPathBulk) {
-        if ((threadIdx.x & 31) == 0)
-            for (uint32_t st = 0; st < kStages; ++st) mbar_init(bar_base + st * 8, 1);
-        fence_mbar_init();
-    }
+    const uint32_t stg_base = smem_addr(smem) + staging_offset + warp_in_block * kWarpCoopBytes;
     __syncthreads();
-    uint32_t wctr = 0, rctr = 0;     // bulk-copy windows issued / consumed by this warp
-    bool failed = false;
 
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t dead = T.enc(A.n);
@@ -257,80 +248,6 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
             if ((PATH == kPathCoop || PATH == kPathCoopSet) && __any_sync(kFull, my_pending)) {
                 const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
                 coop_converge<LUT, true>(T, stg_base, lane, my_pending, p.text, lim, min(end, lim), pos, s, dead);
-            }
-            if (PATH == kPathBulk) {
-                if (__any_sync(kFull, my_pending) && !failed) {
-                    // windows [ws0 + kWin*j, +kWin) of the 16-byte-aligned text; bytes at or past
-                    // `lim` (the text length rounded down to 16) are left to plain loads below
-                    const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
-                    const uint64_t ws0 = pos & ~static_cast<uint64_t>(15);
-                    const uint64_t stop = min(end, lim);
-                    uint32_t j_issue = 0, j_read = 0;
-                    auto issue = [&]() {
-                        const uint32_t stage = wctr % kStages;
-                        const uint32_t bar = bar_base + stage * 8;
-                        const uint64_t ws = ws0 + static_cast<uint64_t>(kWin) * j_issue;
-                        uint32_t bytes = 0;
-                        if (my_pending && s != dead && ws < stop)
-                            bytes = static_cast<uint32_t>(min(static_cast<uint64_t>(kWin), lim - ws));
-                        const uint32_t total = __reduce_add_sync(kFull, bytes);
-                        if (lane == 0) mbar_arrive_expect_tx(bar, total);
-                        __syncwarp();
-                        if (bytes)
-                            bulk_copy_g2s(stg_base + (stage * 32 + lane) * kLaneStride, p.text + ws, bytes, bar);
-                        ++wctr;
-                        ++j_issue;
-                    };
-                    auto wait_stage = [&]() -> bool {
-                        const uint32_t bar = bar_base + (rctr % kStages) * 8;
-                        const uint32_t parity = (rctr / kStages) & 1;
-                        if (!mbar_wait_warp(bar, parity, kSpinLimit)) return false;
-                        ++rctr;
-                        return true;
-                    };
-                    for (uint32_t i = 0; i < kStages; ++i) issue();
-                    for (;;) {
-                        const uint64_t ws = ws0 + static_cast<uint64_t>(kWin) * j_read;
-                        const bool have = my_pending && s != dead && ws < stop;
-                        if (!__any_sync(kFull, have)) break;
-                        const uint32_t stage = rctr % kStages;
-                        if (!wait_stage()) {
-                            failed = true;
-                            break;
-                        }
-                        if (have) {
-                            const uint32_t sb = stg_base + (stage * 32 + lane) * kLaneStride;
-                            const uint64_t lo = max(pos, ws), hi = min(stop, ws + kWin);
-                            if (lo == ws && hi == ws + kWin) {
-#pragma unroll
-                                for (uint32_t g = 0; g < kWin / 16; ++g) s = run_granule(T, s, sb + 16 * g);
-                            } else {
-                                for (uint64_t q = lo; q < hi; ++q)
-                                    s = T.next(s, T.cls_of(lds_u8(sb + static_cast<uint32_t>(q - ws))));
-                            }
-                            pos = hi;
-                        }
-                        ++j_read;
-                        __syncwarp();
-                        fence_proxy_async_smem();
-                        issue();
-                    }
-                    // windows issued past the last one read carry no bytes; consume their phases
-                    while (!failed && rctr < wctr)
-                        if (!wait_stage()) failed = true;
-                    if (failed) {
-                        // a copy did not land within the spin limit: report it, give the copies
-                        // still in flight one more bounded wait each, and leave
-                        if (lane == 0) atomicOr(p.status, kStatusTimeout);
-                        while (rctr < wctr) {
-                            const uint32_t bar = bar_base + (rctr % kStages) * 8;
-                            const uint32_t parity = (rctr / kStages) & 1;
-                            (void)mbar_wait_warp(bar, parity, kSpinLimit);
-                            ++rctr;
-                        }
-                        return;
-                    }
-                }
             }
             if (my_pending) {
                 tail_converge<LUT, PATH == kPathGlobal>(T, p.text, pos, end, s, dead);
@@ -1310,7 +1227,6 @@ cudaError_t reach_m(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, in
 
 cudaError_t reach_dispatch(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
     switch (pl.path) {
-        case kPathBulk: return reach_m<kPathBulk>(a, pl, st, per_sm);
         case kPathCoop: return reach_m<kPathCoop>(a, pl, st, per_sm);
         case kPathCoop2: return reach_m<kPathCoop2>(a, pl, st, per_sm);
         case kPathCoopSet: return reach_m<kPathCoopSet>(a, pl, st, per_sm);
@@ -1358,9 +1274,9 @@ cudaError_t lookback_dispatch(const LookbackArgs &a, int sms, cudaStream_t st) {
 }
 
 // Choose the layout of a reach launch.  Defaults: the smallest lane-replicated table that fits
-// (16-bit, then 32-bit offsets), else the compact table; text staged by bulk copies when the
-// text is 16-byte aligned and the staging ring fits next to the table; one block per SM with
-// as many warps as fit; a grid of one wave.
+// (16-bit, then 32-bit offsets), else the compact table; text staged warp-cooperatively in
+// shared memory when the text is 16-byte aligned and the staging buffers fit next to the table;
+// one block per SM with as many warps as fit; a grid of one wave.
 int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *text,
                const ReachArgs &ra, int sms, ReachPlan *out) {
     ReachPlan pl;
@@ -1423,10 +1339,11 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
         const int w = static_cast<int>(std::min<size_t>(cap2 / 32, room / per_warp));
         return (block == 0 ? w >= 4 : block / 32 <= w) ? w : 0;
     };
-    const int w_coop = fits(kWarpCoopBytes), w_bulk = fits(kWarpStageBytes), w_coop2 = fits2(kWarpCoop2Bytes);
+    const int w_coop = fits(kWarpCoopBytes), w_coop2 = fits2(kWarpCoop2Bytes);
     const int w_set = std::min(w_coop, 512 / 32);
     // auto: one chain per lane with cooperative staging (16-byte-aligned text, buffers fit),
-    // else plain global loads.  (Two chains per lane and bulk copies measured slower on GB300.)
+    // else plain global loads.  (Two chains per lane measured slower on GB300; so did per-lane
+    // bulk copies, a path since retired so that no kernel can leave with a copy in flight.)
     // Automata whose table is too large to replicate are the ones whose runs stay apart: there a
     // lane finishes all of its chunk's runs together (measured on the codon RE: 1.21x; on
     // replicated-table workloads the 512-thread cap of that variant cost 8-13%).
@@ -1436,16 +1353,14 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
                   : !w_coop ? kPathGlobal
                   : many_runs && w_set >= 4 && block <= 512 ? kPathCoopSet : kPathCoop;
     else if (text_path == 1) pl.path = kPathGlobal;
-    else if (text_path == 2) pl.path = kPathBulk;
+    else if (text_path == 2) return RIDFA_E_ARG;   // retired: per-lane bulk copies
     else if (text_path == 3) pl.path = kPathCoop;
     else if (text_path == 4) pl.path = kPathCoop2;
     else pl.path = kPathCoopSet;
-    if (pl.path == kPathBulk && !(aligned && w_bulk)) return RIDFA_E_ARG;
     if (pl.path == kPathCoop && !(aligned && w_coop)) return RIDFA_E_ARG;
     if (pl.path == kPathCoop2 && !(aligned && w_coop2)) return RIDFA_E_ARG;
     if (pl.path == kPathCoopSet && !(aligned && w_set)) return RIDFA_E_ARG;
-    const int warps_fit = pl.path == kPathBulk      ? w_bulk
-                          : pl.path == kPathCoop    ? w_coop
+    const int warps_fit = pl.path == kPathCoop      ? w_coop
                           : pl.path == kPathCoopSet ? w_set
                           : pl.path == kPathCoop2 ? w_coop2
                                                   : cap / 32;
@@ -1453,8 +1368,7 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     const int bcap = pl.path == kPathCoop2 ? cap2 : pl.path == kPathCoopSet ? 512 : cap;
     if (block < 32 || block > bcap || block % 32) return RIDFA_E_ARG;
     pl.block = block;
-    pl.smem = pl.path == kPathBulk    ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpStageBytes
-              : pl.path == kPathCoop || pl.path == kPathCoopSet
+    pl.smem = pl.path == kPathCoop || pl.path == kPathCoopSet
                   ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpCoopBytes
               : pl.path == kPathCoop2 ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpCoop2Bytes
                                       : table_smem;
@@ -1635,6 +1549,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
         if (e != cudaSuccess) return cuda_fail(e);
     }
     // (the groups' launches share the run lists: they run one after another on the stream)
+    NvtxRange reach_range("ridfa reach");
     for (uint32_t g = 0; g < n_launch; ++g) {
         e = lockstep ? piece_dispatch(ras[g], plans[g], sms, st) : reach_dispatch(ras[g], plans[g], st, nullptr);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -1671,6 +1586,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
     if (prof) cudaEventRecord(static_cast<cudaEvent_t>(S->ev[1]), st);
 
     // ---- join
+    NvtxRange join_range("ridfa join");
     ridfa_shard_summary *d_summary =
         h_summary ? reinterpret_cast<ridfa_shard_summary *>(base + L.summary_off) : nullptr;
     JoinArgs ja{A, n_chunks, maps, dinfo, status, partials, ticket, accept, per_thread, d_summary};
@@ -1762,7 +1678,7 @@ int launch_with_buffers(const HostAutomaton &H, const PreparedBuffers &B, const 
 
 namespace ridfa {
 namespace {
-// The bounded wait of the bulk-copy path, exercised alone: one warp waits on a fresh mbarrier for
+// The library's bounded mbarrier wait, exercised alone: one warp waits on a fresh mbarrier for
 // its first phase, at most `limit` polls.  With `arrive` lane 0 completes the phase first; without
 // it nothing ever arrives and the wait must run out.  *status gets kStatusTimeout when it did.
 __global__ void rid_wait_check_kernel(uint32_t limit, int arrive, uint32_t *status) {

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstddef>
 #include <cuda_runtime_api.h>
+#include <nvtx3/nvToolsExt.h>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -12,6 +13,15 @@
 #include "ridfa.h"
 
 namespace ridfa {
+
+// A named NVTX range over a host scope (compile, reach launches, join launch, batch and server
+// launches), for timeline tools such as Nsight Systems; free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // One speculative automaton as the device sees it: the RI-DFA B with its interface
 // (Sec. 3.1-3.4) or the minimal DFA with every state initial (Sec. 2).

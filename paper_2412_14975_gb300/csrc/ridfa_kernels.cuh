@@ -85,23 +85,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Text staging for the converged phase (TMA path): every lane streams its own chunk through a
-// ring of kStages windows of kWin bytes in shared memory, filled by 1-D bulk copies
-// (cp.async.bulk) that complete on one mbarrier per warp and stage.  A lane's window buffers
-// are kLaneStride bytes apart, so the 16-byte reads of 8 consecutive lanes fall in 8 different
-// bank groups (stride 48 = 3 granules, and 3 is odd).
-constexpr uint32_t kWin = 128;
-constexpr uint32_t kStages = 2;
-constexpr uint32_t kLaneStride = 144;
-// per-warp ring + barriers, rounded to 16 bytes so every warp's ring starts 16-byte aligned
-// (bulk-copy destinations must be)
-constexpr uint32_t kWarpStageBytes = (kStages * 32 * kLaneStride + kStages * 8 + 15) & ~15u;
-static_assert(kWarpStageBytes % 16 == 0 && (kStages * 32 * kLaneStride) % 16 == 0 && kLaneStride % 16 == 0,
-              "bulk-copy destinations must stay 16-byte aligned");
-constexpr uint32_t kStatusTimeout = 4u;   // a bounded wait on a copy gave up
+constexpr uint32_t kStatusTimeout = 4u;   // a bounded device wait gave up
 // text paths of the converged phase
 constexpr int kPathGlobal = 0;   // each lane: 16-byte global loads of its own chunk
-constexpr int kPathBulk = 1;     // each lane: 1-D bulk copies into a shared-memory ring
+// (1 was per-lane 1-D bulk copies into a shared-memory ring: retired)
 constexpr int kPathCoop = 2;     // the warp: coalesced loads of 8 chunks' windows per instruction
 constexpr int kPathCoop2 = 3;    // the same with two chunks per lane, interleaved
 constexpr int kPathCoopSet = 4;  // kPathCoop, and a lane finishes all runs its chunk handed off together
@@ -125,9 +112,6 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t tx) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
-}
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -139,13 +123,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         "selp.u32 %0, 1, 0, P1;\n\t}"
         : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
     return ok != 0;
-}
-__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 // Wait, the whole warp together, for the phase of parity `parity` of the mbarrier at `bar`: at
 // most `limit` polls.  False when the limit ran out (the caller reports a timeout and leaves).

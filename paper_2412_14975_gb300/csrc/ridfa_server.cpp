@@ -217,6 +217,7 @@ int grow_slot(ridfa_server *S, Slot &sl, size_t dneed, size_t hneed) {
 
 // Enqueue one batch on a free slot.  On failure the requests are posted with the error.
 void launch(ridfa_server *S, Slot &sl, std::vector<Request> &batch) {
+    NvtxRange range("ridfa server batch");
     std::vector<const ridfa_program *> progs;
     {
         std::lock_guard<std::mutex> lock(S->mu);
