@@ -318,7 +318,23 @@ def build_batch_workload(lib, torch, dev, n_texts, seed):
     return progs, items, total, d, [r for r, _, _ in res], texts
 
 
-def run_batch(args, lib, torch, dev, stream, world, rank):
+def oracle_accepts(res, texts, rid, idx):
+    """Accept bits of texts[i] for i in idx by the oracle (Thompson state-set simulation)."""
+    from oracle.recognizer import SerialRecognizer
+    sers = {}
+    out = {}
+    for i in idx:
+        r = rid[i]
+        if r not in sers:
+            sers[r] = SerialRecognizer(res[r])
+        out[int(i)] = bool(sers[r].accepts(texts[i]))
+    return out
+
+
+def measure_batch(args, lib, torch, dev, stream, world, rank, steps, warmup, oracle_sample=256):
+    """The batched configuration: one CUDA graph over every (text, RE) item, replayed `steps`
+    times; the plain one-text-per-launch path on the same items; accept bits of a seeded sample
+    of items against the oracle."""
     import numpy as np
     t0 = time.perf_counter()
     progs, items, total, d, res, texts = build_batch_workload(lib, torch, dev, args.batch_texts, args.seed)
@@ -328,7 +344,7 @@ def run_batch(args, lib, torch, dev, stream, world, rank):
     b = lib.ridfa_batch_create(progs, items, acc, chunk_len=args.batch_chunk_len)
     create_s = time.perf_counter() - t0
     st = lib.ridfa_batch_get_stats(b)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         lib.ridfa_batch_run(b, stream=stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -338,7 +354,7 @@ def run_batch(args, lib, torch, dev, stream, world, rank):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             lib.ridfa_batch_run(b, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -347,11 +363,13 @@ def run_batch(args, lib, torch, dev, stream, world, rank):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * total * args.steps / (ms / 1e3) / 1e9
+    value = world * total * steps / (ms / 1e3) / 1e9
     got = acc.cpu().numpy().astype(bool)
+    b.close()
     # the plain one-text-per-launch path on the same texts (same chunk length), for comparison
     L = st["chunk_len"]
     acc1 = torch.zeros(1, dtype=torch.uint8, device=dev)
+
     def one_pass():
         for (ptr, n, r, _) in items:
             lib.ridfa_recognize_async(progs[r], ptr, n, max(1, min(n, (n + L - 1) // L)), acc1, stream=stream)
@@ -362,49 +380,47 @@ def run_batch(args, lib, torch, dev, stream, world, rank):
     e1.record(stream)
     torch.cuda.synchronize()
     single_value = total / (e0.elapsed_time(e1) / 1e3) / 1e9
-    # spot check against the single-text path
+    # accept bits of a seeded sample of items against the oracle
+    rid = [it[2] for it in items]
     rng = np.random.Generator(np.random.PCG64(5))
-    sample = rng.choice(len(items), size=min(64, len(items)), replace=False)
-    mism = 0
-    for i in sample:
-        ptr, n, r, _ = items[i]
-        mism += int(lib.ridfa_recognize(progs[r], ptr, n, max(1, min(n, 64)), stream=stream) != got[i])
+    sample = rng.choice(len(items), size=min(oracle_sample, len(items)), replace=False)
+    t0 = time.perf_counter()
+    want = oracle_accepts(res, texts, rid, sample)
+    oracle_s = time.perf_counter() - t0
+    mism = sum(int(want[int(i)] != bool(got[i])) for i in sample)
+    sample_bytes = int(sum(texts[int(i)].size for i in sample))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle.recognizer import SerialRecognizer
-        t0 = time.perf_counter()
-        nb = 0
-        sers = {}
-        for i in range(len(items)):
-            r = items[i][2]
-            if r not in sers:
-                sers[r] = SerialRecognizer(res[r])
-            sers[r].accepts(texts[i])
-            nb += texts[i].size
-            if time.perf_counter() - t0 > 12:
-                break
-        dt = time.perf_counter() - t0
-        cpu = {"value": round(nb / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"the first {nb} bytes of the batch, item by item, Thompson state-set simulation"}
+        cpu = {"value": round(sample_bytes / oracle_s / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(sample)} sampled batch items ({sample_bytes} bytes), Thompson state-set simulation"}
+    return {"value": round(value, 3), "unit": "GB/s", "steps": steps, "warmup": warmup,
+            "ms_per_step": round(ms / steps, 4),
+            "single_text_per_launch_GBps": round(single_value, 3),
+            "batched_over_single": round(value / single_value, 3),
+            "config": {"workload": f"batched: {len(items)} texts, lognormal median 256 KiB sigma 1, "
+                                   f"16 REs (3 single-text + 13 random), half mutated, one CUDA graph",
+                       "total_bytes": total, "chunk_len": L, "chunks": st["total_chunks"],
+                       "launches_in_graph": st["n_launches"], "tasks": st["n_tasks"],
+                       "join_segments": st["n_segments"], "graph": bool(st["graph"]),
+                       "accepted": int(got.sum()), "generate_s": round(gen_s, 1),
+                       "create_s": round(create_s, 2), "l2": "inputs larger than L2, no flush"},
+            "oracle_check": {"items": len(sample), "bytes": sample_bytes, "mismatches": mism,
+                             "accepted": int(sum(want.values()))},
+            "clocks": clk.summary(), "cpu_baseline": cpu,
+            "gpu_launches": steps * st["n_launches"]}
+
+
+def run_batch(args, lib, torch, dev, stream, world, rank):
+    r = measure_batch(args, lib, torch, dev, stream, world, rank, args.steps, args.warmup)
     if rank == 0:
-        line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        line = {"metric": METRIC, "value": r["value"], "unit": "GB/s", "n_gpus": world,
+                "steps": r["steps"], "warmup": r["warmup"], "ms_per_step": r["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-                "data": "synthetic",
-                "config": {"workload": f"batched: {len(items)} texts, lognormal median 256 KiB sigma 1, "
-                                       f"16 REs (3 single-text + 13 random), half mutated, one CUDA graph",
-                           "total_bytes": total, "chunk_len": L, "chunks": st["total_chunks"],
-                           "launches_in_graph": st["n_launches"], "tasks": st["n_tasks"],
-                           "join_segments": st["n_segments"], "graph": bool(st["graph"]),
-                           "accepted": int(got.sum()), "spot_check_mismatches": mism,
-                           "generate_s": round(gen_s, 1), "create_s": round(create_s, 2),
-                           "l2": "inputs larger than L2, no flush"},
-                "single_text_per_launch_GBps": round(single_value, 3),
-                "batched_over_single": round(value / single_value, 3),
-                "clocks": clk.summary(), "cpu_baseline": cpu,
-                "gpu_launches": args.steps * st["n_launches"]}
+                "data": "synthetic", "config": r["config"],
+                "single_text_per_launch_GBps": r["single_text_per_launch_GBps"],
+                "batched_over_single": r["batched_over_single"], "oracle_check": r["oracle_check"],
+                "clocks": r["clocks"], "cpu_baseline": r["cpu_baseline"], "gpu_launches": r["gpu_launches"]}
         print(json.dumps(line), flush=True)
-    b.close()
 
 
 def build_served_workload(lib, n_res, n_pool, seed):
@@ -432,73 +448,53 @@ def build_served_workload(lib, n_res, n_pool, seed):
     return [r for r, _, _ in res], progs, texts, rid
 
 
-def run_served(args, lib, torch, dev, rank):
-    """Open-loop Poisson load on the server at each rate: latency = result posted - scheduled
-    arrival (submit lateness + the server's submit-to-result time), so a client that falls behind
-    is charged for it."""
+def measure_served(args, lib, torch, dev, rank, rates, seconds):
+    """Open-loop Poisson load on the server at each rate, driven by the library's C load
+    generator (ridfa_bench_served_poisson, so the client's cost is not Python's): latency =
+    result posted - scheduled arrival.  Every request's accept bit is checked against the
+    oracle's answer for its text; the one-text-per-launch path on the same mix is timed beside."""
     import numpy as np
     t0 = time.perf_counter()
     res, progs, texts, rid = build_served_workload(lib, 32, args.served_pool, args.seed)
     gen_s = time.perf_counter() - t0
-    rates = [int(r) for r in args.served_rates.split(",")]
-    rng = np.random.Generator(np.random.PCG64(args.seed + 7))
+    t0 = time.perf_counter()
+    want_map = oracle_accepts(res, texts, rid, range(len(texts)))
+    want = np.array([want_map[i] for i in range(len(texts))])
+    oracle_s = time.perf_counter() - t0
     srv = lib.Server(n_streams=3, arena_bytes=4 << 30, max_batch_requests=8192, max_batch_bytes=512 << 20,
-                     chunk_len=args.batch_chunk_len)
+                     chunk_len=args.batch_chunk_len, device_budget=args.served_budget)
     slots = [srv.add_program(p) for p in progs]
-    # correctness: served results equal the single-text path on a sample (warms the server too)
-    sample = rng.choice(len(texts), size=min(64, len(texts)), replace=False)
-    want = {}
-    for i in sample:
-        x = texts[i]
-        if x.size == 0:
-            continue
-        d = torch.from_numpy(x).to(dev)
-        want[int(i)] = lib.ridfa_recognize(progs[rid[i]], d, x.size, max(1, min(x.size, 64)))
-    ids = {srv.submit(slots[rid[i]], texts[i]): i for i in want}
-    srv.drain()
-    mism = 0
-    for r_id, st, acc, _ in srv.poll():
-        mism += int(st != 0 or acc != want[ids[r_id]])
+    pslots = [slots[r] for r in rid]
     lens = np.array([x.size for x in texts])
+    # warm the server (a short run at the lowest rate, unreported)
+    srv.bench_poisson(pslots, texts, rates[0], min(1.0, seconds), args.seed + 99)
     results = []
+    total_mism = 0
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        for rate in rates:
-            n = max(1, int(rate * args.served_seconds))
-            sched = np.cumsum(rng.exponential(1.0 / rate, size=n))
-            pick = rng.integers(0, len(texts), size=n)
-            late = {}
-            lat = []
-            srv_lat = []
+        for q, rate in enumerate(rates):
             st0 = srv.stats()
-            nbytes = 0
-            i = 0
-            tstart = time.perf_counter()
-            while i < n or len(lat) < n:
-                now = time.perf_counter() - tstart
-                if i < n and now >= sched[i]:
-                    j = int(pick[i])
-                    r_id = srv.try_submit(slots[rid[j]], texts[j])
-                    if r_id is not None:
-                        late[r_id] = now - sched[i]
-                        nbytes += texts[j].size
-                        i += 1
-                        continue
-                for r_id, st, acc, us in srv.poll(wait_us=0 if i < n else 1000):
-                    lat.append(late.pop(r_id) * 1e3 + us / 1e3)
-                    srv_lat.append(us / 1e3)
-            wall = time.perf_counter() - tstart
+            recs, wall = srv.bench_poisson(pslots, texts, rate, seconds, args.seed + 7 + q)
             st1 = srv.stats()
-            lat = np.sort(np.array(lat))
+            lat = np.sort(recs["latency_us"] / 1e3)
+            slat = np.sort(recs["server_us"] / 1e3)
+            mism = int(np.count_nonzero((recs["status"] != 0) |
+                                        (recs["accept"].astype(bool) != want[recs["text"]])))
+            total_mism += mism
             nb = st1["batches"] - st0["batches"]
-            results.append({"offered_rps": rate, "requests": n, "achieved_rps": round(n / wall, 1),
+            hist = [a - b for a, b in zip(st1["batch_hist"], st0["batch_hist"])]
+            nbytes = int(lens[recs["text"]].sum())
+            results.append({"offered_rps": rate, "requests": int(len(recs)),
+                            "achieved_rps": round(len(recs) / wall, 1),
                             "GBps": round(nbytes / wall / 1e9, 3),
                             "p50_ms": round(float(np.percentile(lat, 50)), 3),
                             "p99_ms": round(float(np.percentile(lat, 99)), 3),
                             "max_ms": round(float(lat[-1]), 3),
-                            "server_p50_ms": round(float(np.percentile(srv_lat, 50)), 3),
-                            "server_p99_ms": round(float(np.percentile(srv_lat, 99)), 3), "batches": nb,
-                            "mean_batch": round(n / max(nb, 1), 1),
-                            "busy_retries": st1["rejected"] - st0["rejected"]})
+                            "server_p50_ms": round(float(np.percentile(slat, 50)), 3),
+                            "server_p99_ms": round(float(np.percentile(slat, 99)), 3),
+                            "batches": nb, "mean_batch": round(len(recs) / max(nb, 1), 1),
+                            "batch_hist_log2": hist[:max([i + 1 for i, h in enumerate(hist) if h] or [1])],
+                            "busy_retries": int(recs["busy_retries"].sum()),
+                            "oracle_mismatches": mism})
     stats = srv.stats()
     srv.close()
     # one text per launch on the same request mix: copy, recognise, read the bit, one by one
@@ -515,25 +511,36 @@ def run_served(args, lib, torch, dev, rank):
         d_buf[:n].copy_(h, non_blocking=True)
         lib.ridfa_recognize(progs[rid[j]], d_buf, n, max(1, min(n, (n + L - 1) // L)))
         nb1 += n
-    single = {"requests": len(pin), "GBps": round(nb1 / (time.perf_counter() - t0) / 1e9, 3),
-              "rps": round(len(pin) / (time.perf_counter() - t0), 1)}
-    ref = next((r for r in results if r["offered_rps"] == args.served_ref_rate), results[-1])
+    dt1 = time.perf_counter() - t0
+    single = {"requests": len(pin), "GBps": round(nb1 / dt1 / 1e9, 3), "rps": round(len(pin) / dt1, 1)}
+    return {"rates": results, "seconds_per_rate": seconds, "single_text_per_launch": single,
+            "config": {"workload": f"served: Poisson arrivals over {len(res)} resident REs, host texts "
+                                   f"lognormal median 64 KiB sigma 1 (max 16 MiB), {seconds} s per rate",
+                       "pool_texts": len(texts), "pool_mean_bytes": int(lens.mean()),
+                       "generate_s": round(gen_s, 1), "n_streams": 3,
+                       "device_budget": args.served_budget or None,
+                       "chunk_len": args.batch_chunk_len or "adaptive (1-8 KiB per batch)",
+                       "client": "ridfa_bench_served_poisson (C, open loop)"},
+            "oracle_check": {"requests": int(sum(r["requests"] for r in results)), "mismatches": total_mism,
+                             "pool_oracle_s": round(oracle_s, 1)},
+            "server_stats": stats, "clocks": clk.summary()}
+
+
+def run_served(args, lib, torch, dev, rank):
+    rates = [int(r) for r in args.served_rates.split(",")]
+    r = measure_served(args, lib, torch, dev, rank, rates, args.served_seconds)
+    ref = next((x for x in r["rates"] if x["offered_rps"] == args.served_ref_rate), r["rates"][-1])
     if rank == 0:
+        cfg = dict(r["config"])
+        cfg["workload"] += f"; value = p99 at {ref['offered_rps']} req/s"
         line = {"metric": METRIC, "value": ref["p99_ms"], "unit": "ms", "n_gpus": 1,
                 "steps": len(rates), "warmup": args.warmup, "ms_per_step": None,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-                "data": "synthetic",
-                "config": {"workload": f"served: Poisson arrivals over {len(res)} resident REs, host texts "
-                                       f"lognormal median 64 KiB sigma 1 (max 16 MiB), {args.served_seconds} s "
-                                       f"per rate; value = p99 at {ref['offered_rps']} req/s",
-                           "pool_texts": len(texts), "pool_mean_bytes": int(lens.mean()),
-                           "generate_s": round(gen_s, 1), "n_streams": 3,
-                           "chunk_len": args.batch_chunk_len or "adaptive (1-8 KiB per batch)",
-                           "correctness_sample": len(want), "mismatches": mism},
-                "rates": results, "single_text_per_launch": single,
-                "server_stats": stats, "clocks": clk.summary(),
-                "e2e": {"value": ref["GBps"], "unit": "GB/s", "h2d_bytes_per_step": int(lens.mean()),
-                        "d2h_bytes_per_step": 1},
+                "data": "synthetic", "config": cfg,
+                "rates": r["rates"], "single_text_per_launch": r["single_text_per_launch"],
+                "oracle_check": r["oracle_check"], "server_stats": r["server_stats"], "clocks": r["clocks"],
+                "e2e": {"value": ref["GBps"], "unit": "GB/s",
+                        "h2d_bytes_per_step": r["config"]["pool_mean_bytes"], "d2h_bytes_per_step": 1},
                 "gpu_launches": None}
         print(json.dumps(line), flush=True)
 
@@ -545,9 +552,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["batch", "served"])
-    ap.add_argument("--served-rates", default="2000,5000,10000,20000,50000,100000,200000")
-    ap.add_argument("--served-seconds", type=float, default=5.0)
+    ap.add_argument("--served-rates", default="2000,5000,10000,20000,50000",
+                    help="--workload served: Poisson rates (req/s)")
+    ap.add_argument("--served-seconds", type=float, default=60.0,
+                    help="--workload served: seconds of arrivals per rate (the configured 60 s)")
     ap.add_argument("--served-ref-rate", type=int, default=10000)
+    ap.add_argument("--served-budget", type=int, default=0,
+                    help="server device budget in bytes (tables + texts + scratch; 0 = none)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload: skip the batched configuration's measurement")
+    ap.add_argument("--no-served", action="store_true",
+                    help="default workload: skip the served configuration's measurement")
+    ap.add_argument("--combined-batch-steps", type=int, default=10)
+    ap.add_argument("--combined-served-rates", default="2000,10000,50000")
+    ap.add_argument("--combined-served-seconds", type=float, default=10.0)
     ap.add_argument("--served-pool", type=int, default=2048)
     ap.add_argument("--batch-texts", type=int, default=10000)
     ap.add_argument("--batch-chunk-len", type=int, default=0, help="0 = autotune")
@@ -565,7 +583,7 @@ def main():
     ap.add_argument("--piece-len", type=int, default=0,
                     help="intra-chunk speculation piece length (0 auto, 1 off, >= 64 bytes)")
     ap.add_argument("--text-path", type=int, default=0,
-                    help="converged-phase text reads (0 auto, 1 global loads, 2 bulk-copy staging)")
+                    help="converged-phase text reads (0 auto, 1 global loads, 3 cooperative staging, 4 two chunks per lane, 5 set path)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -771,6 +789,21 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(name, re_src)
 
+    # the other two numbers of the metric, on the same GPU in the same run (one GPU only: under
+    # torchrun every rank measures its single-text replica alone)
+    batched = served = None
+    if name == "c3" and world == 1 and args.text_bytes is None:
+        del d_text
+        torch.cuda.empty_cache()
+        if not args.no_batched:
+            batched = measure_batch(args, lib, torch, dev, stream, world, rank,
+                                    args.combined_batch_steps, args.warmup)
+            torch.cuda.empty_cache()
+        if not args.no_served:
+            served = measure_served(args, lib, torch, dev, rank,
+                                    [int(r) for r in args.combined_served_rates.split(",")],
+                                    args.combined_served_seconds)
+
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -786,6 +819,7 @@ def main():
                 "dfa_value": round(dfa_value, 3) if dfa_value else None,
                 "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "work": work,
                 "interface_ablation": ablation,
+                "batched": batched, "served": served,
                 "gpu_launches": 2 * args.steps}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -371,6 +371,12 @@ typedef struct {
     uint32_t chunk_len;         /* bytes per chunk; 0 = adapted per batch: about two chunks per
                                    resident lane of the GPU, a power of two in [1 KiB, 8 KiB] */
     uint32_t reserved;
+    uint64_t device_budget;     /* admission by device memory: the resident programs' tables plus,
+                                   for every admitted and unfinished request, its arena text and
+                                   its kernel scratch (chunk maps and summaries, 2k + 4 bytes per
+                                   chunk of at least chunk_len -- 1 KiB when adaptive -- plus 64)
+                                   may not exceed this many bytes; 0 = no budget (the arena and
+                                   max_requests alone admit) */
 } ridfa_server_opts;
 
 typedef struct {
@@ -384,6 +390,11 @@ typedef struct {
     uint64_t submitted, completed, rejected, batches, bytes;
     uint32_t max_batch, n_programs;
     uint64_t device_bytes;      /* arena + slot scratch */
+    uint64_t table_bytes;       /* device tables of the resident programs (charged to the budget) */
+    uint64_t budget_used;       /* tables + admitted unfinished requests, now */
+    uint64_t budget_peak;       /* ... and its largest value so far */
+    uint32_t batch_hist[16];    /* batches by size: bucket b counts batches of 2^b .. 2^(b+1)-1
+                                   requests (the last bucket: 2^15 and more) */
 } ridfa_server_stats;
 
 typedef struct ridfa_server ridfa_server;
@@ -396,13 +407,21 @@ typedef struct ridfa_server ridfa_server;
 int ridfa_server_create(const ridfa_server_opts *opts, ridfa_server **out);
 
 /* Make `prog` resident (tables uploaded now) and return its slot for submit().  The program
- * must outlive the server.  Errors: E_ARG, E_UNSUPPORTED (k > RIDFA_MAX_SLOTS), E_NOMEM, E_CUDA. */
+ * must outlive the server.  With a device_budget its table bytes (ridfa_info.table_bytes) are
+ * charged to the budget for the server's life; E_BUSY when they do not fit beside what is
+ * already charged (nothing is added then).
+ * Errors: E_ARG, E_UNSUPPORTED (k > RIDFA_MAX_SLOTS), E_BUSY, E_NOMEM, E_CUDA. */
 int ridfa_server_add_program(ridfa_server *srv, const ridfa_program *prog, uint32_t *prog_slot);
 
 /* Submit one request: recognise text[0, len) with program `prog_slot`.  A host text is copied
  * before the call returns; a device text (RIDFA_SUBMIT_DEVICE_TEXT) is read in place.
- * Errors: E_ARG, E_BUSY (arena or request budget full: poll, then retry), E_TOO_LARGE (the text
- * alone exceeds the arena or a batch). */
+ * Admission: the arena must have room for a host text, fewer than max_requests may be
+ * outstanding, and with a device_budget the request's charge (its arena text, none for a device
+ * text, plus its scratch) must fit beside the tables and the requests still unfinished; the
+ * charge is released when the result is posted.
+ * Errors: E_ARG, E_BUSY (arena, request count or device budget full: poll, then retry),
+ * E_TOO_LARGE (the text alone exceeds the arena or a batch, or its charge exceeds the budget
+ * left beside the tables). */
 int ridfa_server_submit(ridfa_server *srv, uint32_t prog_slot, const uint8_t *text, uint64_t len,
                         uint32_t flags, uint64_t *req_id);
 
@@ -418,6 +437,32 @@ int ridfa_server_get_stats(const ridfa_server *srv, ridfa_server_stats *out);
 
 /* Stop the scheduler, wait for work in flight and release everything.  NULL is a no-op. */
 void ridfa_server_destroy(ridfa_server *srv);
+
+/* Open-loop Poisson load generator for a server (a measurement client; the paper has no
+ * counterpart).  Arrivals at rate_rps for `seconds` (exponential gaps, seeded); each arrival
+ * submits a uniformly chosen text of the caller's pool (host texts, copied into the arena) with
+ * its program slot, retrying while the server answers E_BUSY, and polls results in between.
+ * Latency of a request = (submit time - scheduled arrival) + the server's submit-to-result time,
+ * so a client or server that falls behind is charged for it.  Runs on the calling thread and
+ * returns when every request's result has been polled.
+ *   prog_slots[i], texts[i], lens[i]: the pool (n_texts entries); records: out[0..cap), one per
+ *   request in arrival order (*n_out of them); *wall_s: seconds from the first arrival to the
+ *   last result.
+ * Errors: E_ARG (bad arguments, or more arrivals than cap), E_TOO_LARGE, errors of submit. */
+typedef struct {
+    uint32_t text;              /* pool index of the request's text */
+    int32_t status;             /* the request's result status */
+    uint32_t accept;            /* 1 if accepted */
+    uint32_t busy_retries;      /* submits refused with E_BUSY before this one was admitted */
+    double latency_us;          /* scheduled arrival to result posted */
+    double server_us;           /* submit to result posted (the server's own measure) */
+} ridfa_loadgen_record;
+
+int ridfa_bench_served_poisson(ridfa_server *srv, const uint32_t *prog_slots,
+                               const uint8_t *const *texts, const uint64_t *lens, uint32_t n_texts,
+                               double rate_rps, double seconds, uint64_t seed,
+                               ridfa_loadgen_record *out, uint32_t cap, uint32_t *n_out,
+                               double *wall_s);
 
 /* Roofline microbenchmarks (diagnostics; the paper has no counterpart).  Both allocate a 4-byte
  * sink and synchronise the current device.

@@ -394,7 +394,7 @@ RIDFA_SUBMIT_DEVICE_TEXT = 1
 class ServerOpts(_c.Structure):
     _fields_ = [("device", _c.c_int32), ("n_streams", _u32), ("arena_bytes", _c.c_uint64),
                 ("max_requests", _u32), ("max_batch_requests", _u32), ("max_batch_bytes", _c.c_uint64),
-                ("chunk_len", _u32), ("reserved", _u32)]
+                ("chunk_len", _u32), ("reserved", _u32), ("device_budget", _c.c_uint64)]
 
 
 class Result(_c.Structure):
@@ -405,10 +405,18 @@ class Result(_c.Structure):
 class ServerStats(_c.Structure):
     _fields_ = [("submitted", _c.c_uint64), ("completed", _c.c_uint64), ("rejected", _c.c_uint64),
                 ("batches", _c.c_uint64), ("bytes", _c.c_uint64), ("max_batch", _u32),
-                ("n_programs", _u32), ("device_bytes", _c.c_uint64)]
+                ("n_programs", _u32), ("device_bytes", _c.c_uint64), ("table_bytes", _c.c_uint64),
+                ("budget_used", _c.c_uint64), ("budget_peak", _c.c_uint64), ("batch_hist", _u32 * 16)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "batch_hist"}
+        d["batch_hist"] = list(self.batch_hist)
+        return d
+
+
+class LoadgenRecord(_c.Structure):
+    _fields_ = [("text", _u32), ("status", _c.c_int32), ("accept", _u32), ("busy_retries", _u32),
+                ("latency_us", _c.c_double), ("server_us", _c.c_double)]
 
 
 _decl("ridfa_server_create", _c.c_int, [_c.POINTER(ServerOpts), _c.POINTER(_vp)])
@@ -418,6 +426,9 @@ _decl("ridfa_server_poll", _c.c_int, [_vp, _c.POINTER(Result), _u32, _c.POINTER(
 _decl("ridfa_server_drain", _c.c_int, [_vp, _u32])
 _decl("ridfa_server_get_stats", _c.c_int, [_vp, _c.POINTER(ServerStats)])
 _decl("ridfa_server_destroy", None, [_vp])
+_decl("ridfa_bench_served_poisson", _c.c_int, [_vp, _vp, _vp, _vp, _u32, _c.c_double, _c.c_double,
+                                                _c.c_uint64, _c.POINTER(LoadgenRecord), _u32,
+                                                _c.POINTER(_u32), _c.POINTER(_c.c_double)])
 
 
 class Server:
@@ -428,9 +439,10 @@ class Server:
     device=True (read in place: keep it alive until its result is polled)."""
 
     def __init__(self, device=-1, n_streams=0, arena_bytes=0, max_requests=0, max_batch_requests=0,
-                 max_batch_bytes=0, chunk_len=0):
+                 max_batch_bytes=0, chunk_len=0, device_budget=0):
         opts = ServerOpts(int(device), int(n_streams), int(arena_bytes), int(max_requests),
-                          int(max_batch_requests), int(max_batch_bytes), int(chunk_len), 0)
+                          int(max_batch_requests), int(max_batch_bytes), int(chunk_len), 0,
+                          int(device_budget))
         h = _vp()
         _check(_lib.ridfa_server_create(_c.byref(opts), _c.byref(h)), "ridfa_server_create")
         self.handle = h.value
@@ -479,6 +491,26 @@ class Server:
 
     def drain(self, timeout_ms=60_000):
         _check(_lib.ridfa_server_drain(self, int(timeout_ms)), "ridfa_server_drain")
+
+    def bench_poisson(self, prog_slots, texts, rate_rps, seconds, seed):
+        """ridfa_bench_served_poisson over a pool of host texts (contiguous uint8 numpy arrays,
+        one program slot each).  Returns (records as a structured numpy array, wall seconds)."""
+        n = len(texts)
+        bufs = [np.ascontiguousarray(t, dtype=np.uint8) for t in texts]
+        ptrs = (_vp * n)(*[b.ctypes.data if b.size else None for b in bufs])
+        lens = (_c.c_uint64 * n)(*[int(b.size) for b in bufs])
+        slots = (_u32 * n)(*[int(p) for p in prog_slots])
+        cap = int(rate_rps * seconds * 1.5) + 1000
+        recs = (LoadgenRecord * cap)()
+        n_out, wall = _u32(), _c.c_double()
+        _check(_lib.ridfa_bench_served_poisson(self, slots, ptrs, lens, n, float(rate_rps), float(seconds),
+                                               int(seed), recs, cap, _c.byref(n_out), _c.byref(wall)),
+               "ridfa_bench_served_poisson")
+        out = np.frombuffer(recs, dtype=np.dtype([("text", "<u4"), ("status", "<i4"), ("accept", "<u4"),
+                                                  ("busy_retries", "<u4"), ("latency_us", "<f8"),
+                                                  ("server_us", "<f8")]), count=n_out.value).copy()
+        del bufs
+        return out, wall.value
 
     def stats(self):
         st = ServerStats()

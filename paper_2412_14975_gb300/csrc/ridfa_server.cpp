@@ -15,13 +15,16 @@
 // the arena ranges released.
 #include <cuda_runtime_api.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <mutex>
 #include <new>
+#include <random>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "ridfa.h"
@@ -45,8 +48,16 @@ struct Request {
     uint64_t len = 0;
     uint64_t arena_seq = kNoArena;    // ring entry holding the text
     uint64_t arena_off = 0;
+    uint64_t charge = 0;              // bytes charged to the device budget until posted
     Clock::time_point t0;
 };
+
+// Device bytes of a program's tables as uploaded (the same count as ridfa_info.table_bytes).
+uint64_t table_bytes_of(const ridfa_program *prog) {
+    const HostAutomaton &A = prog->rid;
+    return static_cast<uint64_t>(A.trans.size() * 2 + 256 + A.final_bits.size() * 4 + A.ifmask.size() * 4 +
+                                 A.slot_state.size() * 2);
+}
 
 // Ring allocator over [0, cap): ranges are handed out in order and released in any order; space
 // is reclaimed from the oldest live range forward.
@@ -143,6 +154,7 @@ struct ridfa_server {
     std::deque<ridfa::Request> pending;
     std::deque<ridfa_result> done;
     uint64_t next_id = 1, outstanding = 0, in_flight = 0;
+    uint64_t tables = 0, charged = 0;              // device budget: resident tables, requests
     ridfa_server_stats stats{};
     size_t slot_bytes = 0;
     bool stop = false;
@@ -178,6 +190,7 @@ void post(ridfa_server *S, const std::vector<Request> &reqs, int rs, const uint8
         res.latency_us = std::chrono::duration<double, std::micro>(now - r.t0).count();
         S->done.push_back(res);
         if (r.arena_seq != kNoArena) S->ring.release(r.arena_seq);
+        S->charged -= r.charge;
         --S->in_flight;
         ++S->stats.completed;
     }
@@ -290,6 +303,9 @@ void launch(ridfa_server *S, Slot &sl, std::vector<Request> &batch) {
         std::lock_guard<std::mutex> lock(S->mu);
         ++S->stats.batches;
         if (n > S->stats.max_batch) S->stats.max_batch = n;
+        uint32_t b = 0;
+        while (b < 15 && (2u << b) <= n) ++b;
+        ++S->stats.batch_hist[b];
     }
     sl.reqs.swap(batch);
     sl.busy = true;
@@ -389,7 +405,7 @@ extern "C" int ridfa_server_create(const ridfa_server_opts *opts, ridfa_server *
     if (!out) return RIDFA_E_ARG;
     ridfa_server *S = new (std::nothrow) ridfa_server();
     if (!S) return RIDFA_E_NOMEM;
-    ridfa_server_opts o = opts ? *opts : ridfa_server_opts{-1, 0, 0, 0, 0, 0, 0, 0};
+    ridfa_server_opts o = opts ? *opts : ridfa_server_opts{-1, 0, 0, 0, 0, 0, 0, 0, 0};
     if (o.device < 0) {
         int d = 0;
         if (cudaGetDevice(&d) != cudaSuccess) {
@@ -457,6 +473,14 @@ extern "C" int ridfa_server_add_program(ridfa_server *S, const ridfa_program *pr
         if (!ridfa::device_copy(prog, false, S->device, &err)) return err;
     }
     std::lock_guard<std::mutex> lock(S->mu);
+    const uint64_t tb = ridfa::table_bytes_of(prog);
+    if (S->o.device_budget && S->tables + S->charged + tb > S->o.device_budget) {
+        ++S->stats.rejected;
+        return RIDFA_E_BUSY;
+    }
+    S->tables += tb;
+    S->stats.table_bytes = S->tables;
+    S->stats.budget_peak = std::max(S->stats.budget_peak, S->tables + S->charged);
     *prog_slot = static_cast<uint32_t>(S->progs.size());
     S->progs.push_back(prog);
     S->stats.n_programs = static_cast<uint32_t>(S->progs.size());
@@ -478,6 +502,19 @@ extern "C" int ridfa_server_submit(ridfa_server *S, uint32_t prog_slot, const ui
             ++S->stats.rejected;
             return RIDFA_E_BUSY;
         }
+        if (S->o.device_budget) {
+            // the arena text (a device text is the caller's) and the kernels' per-chunk scratch:
+            // chunk maps (k entries of 2 bytes) and summaries (4 bytes), chunks of at least
+            // chunk_len bytes (1 KiB when adaptive), plus descriptors
+            const uint64_t L = S->o.chunk_len ? S->o.chunk_len : 1024;
+            const uint64_t chunks = len ? (len + L - 1) / L : 0;
+            r.charge = (on_device ? 0 : ridfa::round16(len)) + chunks * (2ull * S->progs[prog_slot]->rid.k + 4) + 64;
+            if (S->tables + r.charge > S->o.device_budget) return RIDFA_E_TOO_LARGE;
+            if (S->tables + S->charged + r.charge > S->o.device_budget) {
+                ++S->stats.rejected;
+                return RIDFA_E_BUSY;
+            }
+        }
         if (!on_device && len) {
             uint64_t off = 0, seq = 0;
             if (!S->ring.alloc(len, &off, &seq)) {
@@ -492,6 +529,8 @@ extern "C" int ridfa_server_submit(ridfa_server *S, uint32_t prog_slot, const ui
         }
         r.id = S->next_id++;
         r.prog = prog_slot;
+        S->charged += r.charge;
+        S->stats.budget_peak = std::max(S->stats.budget_peak, S->tables + S->charged);
         ++S->outstanding;
         ++S->stats.submitted;
     }
@@ -537,6 +576,8 @@ extern "C" int ridfa_server_get_stats(const ridfa_server *S, ridfa_server_stats 
     std::lock_guard<std::mutex> lock(M->mu);
     *out = M->stats;
     out->device_bytes = M->o.arena_bytes + M->slot_bytes;
+    out->table_bytes = M->tables;
+    out->budget_used = M->tables + M->charged;
     return RIDFA_OK;
 }
 
@@ -550,4 +591,78 @@ extern "C" void ridfa_server_destroy(ridfa_server *S) {
     if (S->th.joinable()) S->th.join();
     ridfa::release_server(S);
     delete S;
+}
+
+extern "C" int ridfa_bench_served_poisson(ridfa_server *S, const uint32_t *prog_slots,
+                                          const uint8_t *const *texts, const uint64_t *lens, uint32_t n_texts,
+                                          double rate_rps, double seconds, uint64_t seed,
+                                          ridfa_loadgen_record *out, uint32_t cap, uint32_t *n_out,
+                                          double *wall_s) {
+    using ridfa::Clock;
+    if (!S || !prog_slots || !texts || !lens || !n_texts || !(rate_rps > 0) || !(seconds > 0) || !out ||
+        !n_out)
+        return RIDFA_E_ARG;
+    // the arrival schedule and the text picks, drawn before the clock starts
+    std::mt19937_64 rng(seed);
+    std::exponential_distribution<double> gap(rate_rps);
+    std::uniform_int_distribution<uint32_t> pick(0, n_texts - 1);
+    std::vector<double> sched;
+    std::vector<uint32_t> which;
+    for (double t = gap(rng); t < seconds; t += gap(rng)) {
+        if (sched.size() == cap) return RIDFA_E_ARG;
+        sched.push_back(t);
+        which.push_back(pick(rng));
+    }
+    const size_t n = sched.size();
+    for (size_t i = 0; i < n; ++i) out[i] = ridfa_loadgen_record{which[i], 0, 0, 0, 0.0, 0.0};
+    std::unordered_map<uint64_t, size_t> of_req;
+    of_req.reserve(n * 2 + 16);
+    std::vector<double> submit_s(n, 0.0);
+    std::vector<ridfa_result> res(4096);
+    size_t next = 0, got = 0;
+    int err = RIDFA_OK;
+    const Clock::time_point t0 = Clock::now();
+    auto now_s = [&] { return std::chrono::duration<double>(Clock::now() - t0).count(); };
+    auto drain_results = [&](uint32_t wait_us) {
+        uint32_t m = 0;
+        const int e = ridfa_server_poll(S, res.data(), static_cast<uint32_t>(res.size()), &m, wait_us);
+        if (e != RIDFA_OK) return e;
+        for (uint32_t q = 0; q < m; ++q) {
+            auto it = of_req.find(res[q].req_id);
+            if (it == of_req.end()) continue;        // not one of this run's requests
+            const size_t i = it->second;
+            of_req.erase(it);
+            ridfa_loadgen_record &rec = out[i];
+            rec.status = res[q].status;
+            rec.accept = res[q].accept;
+            rec.server_us = res[q].latency_us;
+            rec.latency_us = (submit_s[i] - sched[i]) * 1e6 + res[q].latency_us;
+            ++got;
+        }
+        return RIDFA_OK;
+    };
+    while (err == RIDFA_OK && (next < n || got < n)) {
+        if (next < n && now_s() >= sched[next]) {
+            const uint32_t j = which[next];
+            uint64_t id = 0;
+            const int e = ridfa_server_submit(S, prog_slots[j], texts[j], lens[j], 0, &id);
+            if (e == RIDFA_OK) {
+                submit_s[next] = now_s();
+                of_req.emplace(id, next);
+                ++next;
+                continue;
+            }
+            if (e != RIDFA_E_BUSY) {
+                err = e;
+                break;
+            }
+            ++out[next].busy_retries;                // full: collect results, then retry
+            err = drain_results(50);
+            continue;
+        }
+        err = drain_results(next < n ? 0 : 1000);
+    }
+    if (wall_s) *wall_s = now_s();
+    *n_out = static_cast<uint32_t>(next);
+    return err;
 }

@@ -146,3 +146,72 @@ def test_served_device_texts_and_admission():
         assert srv.try_submit(slots[0], x) is not None     # room again after polling
         srv.drain()
         assert len(collect(srv, 1)) == 1
+
+
+def test_served_device_budget_counts_tables_and_texts():
+    """Admission by device memory: resident tables are charged to the budget for the server's
+    life; a request is charged its arena text plus its kernels' scratch until its result is
+    posted.  Tables that fill the budget leave no room for texts; a program that does not fit
+    is refused; charges come back when results are polled."""
+    progs = [lib.ridfa_compile(r) for r in RES]
+    tb = [p.info["table_bytes"] for p in progs]
+    x = np.ascontiguousarray(make_text(1, 8192, np.random.Generator(np.random.PCG64(3))))
+    # a request of the record-line RE: its 16-byte-rounded text plus 2k + 4 bytes per 1 KiB chunk
+    k1 = progs[1].info["k"]
+    charge = ((x.size + 15) & ~15) + ((x.size + 1023) // 1024) * (2 * k1 + 4) + 64
+    budget = sum(tb) + 3 * charge + charge // 2          # room for three such requests in flight
+    with lib.Server(n_streams=1, arena_bytes=1 << 20, chunk_len=1024, device_budget=budget) as srv:
+        slots = [srv.add_program(p) for p in progs]
+        st = srv.stats()
+        assert st["table_bytes"] == sum(tb) and st["budget_used"] == sum(tb)
+        # texts until the budget refuses; at most three fit (the arena alone would take ~120)
+        admitted = []
+        while True:
+            rid = srv.try_submit(slots[1], x)
+            if rid is None:
+                break
+            admitted.append(rid)
+            assert len(admitted) <= 3
+        assert 1 <= len(admitted) <= 3
+        assert srv.stats()["budget_used"] <= budget
+        srv.drain()
+        got = collect(srv, len(admitted))
+        assert set(got) == set(admitted) and all(v == want(1, x) for v in got.values())
+        st = srv.stats()
+        assert st["budget_used"] == sum(tb) and st["budget_peak"] <= budget
+        assert srv.try_submit(slots[1], x) is not None    # the charges came back
+        srv.drain()
+        collect(srv, 1)
+        # a text whose charge exceeds what the tables leave can never be admitted
+        with pytest.raises(lib.RidfaError) as e:
+            srv.submit(slots[1], np.zeros(4 * charge, np.uint8))
+        assert e.value.code == -12
+    # tables alone fill a budget: no further program fits and no text is admitted at all
+    with lib.Server(n_streams=1, arena_bytes=1 << 20, device_budget=sum(tb)) as srv:
+        slots = [srv.add_program(p) for p in progs]
+        with pytest.raises(lib.RidfaError) as e:
+            srv.add_program(lib.ridfa_compile("(ab|c)*"))
+        assert e.value.code == -8
+        assert srv.stats()["n_programs"] == len(progs)
+        with pytest.raises(lib.RidfaError) as e:
+            srv.submit(slots[0], b"ACGT")
+        assert e.value.code == -12
+
+
+def test_served_poisson_load_generator():
+    """The C load generator: every request of an open-loop Poisson run gets a result equal to the
+    oracle's, batches form (histogram), and latencies are at least the server's own."""
+    work = [(r, x) for r, x in workload(8, 60) if x.size]
+    expect = np.array([want(r, x) for r, x in work])
+    progs = [lib.ridfa_compile(r) for r in RES]
+    with lib.Server(n_streams=3, arena_bytes=64 << 20) as srv:
+        slots = [srv.add_program(p) for p in progs]
+        recs, wall = srv.bench_poisson([slots[r] for r, _ in work], [x for _, x in work],
+                                       rate_rps=20000, seconds=0.5, seed=11)
+        assert 8000 <= len(recs) <= 12000 and wall >= 0.45
+        assert (recs["status"] == 0).all()
+        assert np.array_equal(recs["accept"].astype(bool), expect[recs["text"]])
+        assert (recs["latency_us"] >= recs["server_us"] - 1.0).all()
+        st = srv.stats()
+        assert st["completed"] == len(recs)
+        assert sum(st["batch_hist"]) == st["batches"] and sum(st["batch_hist"][1:]) > 0
