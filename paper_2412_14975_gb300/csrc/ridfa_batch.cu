@@ -202,14 +202,12 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_batch_kernel(BatchReachArg
                     lim = td.len & ~static_cast<uint64_t>(15);
                     tx = td.text;
                 }
-                coop_converge_set(T, stg_base, lane, m != 0, tx, lim, min(end, lim), pos, stv, m, dead);
+                uint32_t rep = 0xFFFFFFFFu;            // group g -> its slot (4 bits; 0xF dead)
 #pragma unroll
-                for (int g = 0; g < kMaxRun; ++g) {
-                    if (g >= static_cast<int>(m)) continue;
-                    uint64_t pg = pos;
-                    tail_converge<LUT, false>(T, tx, pg, end, stv[g], dead);
-                    wfin[run0 + g] = stv[g];
-                }
+                for (int g = 0; g < kMaxRun; ++g)
+                    if (g < static_cast<int>(m)) rep = (rep & ~(0xFu << (4 * g))) | (static_cast<uint32_t>(g) << (4 * g));
+                coop_converge_set(T, stg_base, lane, m != 0, tx, lim, min(end, lim), pos, stv, rep, dead);
+                if (m) finish_set_runs(T, tx, pos, end, stv, rep, m, wfin + run0, dead);
             }
             for (uint32_t rb = 0; rb < (set_path ? 0u : nruns); rb += 32) {
                 const uint32_t idx = rb + lane;

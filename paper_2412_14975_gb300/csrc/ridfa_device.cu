@@ -217,14 +217,12 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
                 end = chunk_begin(chunk0 + lane + 1, p.len, p.c);
             }
             const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
-            coop_converge_set(T, stg_base, lane, m != 0, p.text, lim, min(end, lim), pos, st, m, dead);
+            uint32_t rep = 0xFFFFFFFFu;                // group g -> its slot (4 bits; 0xF dead)
 #pragma unroll
-            for (int g = 0; g < kMaxRun; ++g) {
-                if (g >= static_cast<int>(m)) continue;
-                uint64_t pg = pos;
-                tail_converge<LUT, false>(T, p.text, pg, end, st[g], dead);
-                wfin[run0 + g] = st[g];
-            }
+            for (int g = 0; g < kMaxRun; ++g)
+                if (g < static_cast<int>(m)) rep = (rep & ~(0xFu << (4 * g))) | (static_cast<uint32_t>(g) << (4 * g));
+            coop_converge_set(T, stg_base, lane, m != 0, p.text, lim, min(end, lim), pos, st, rep, dead);
+            if (m) finish_set_runs(T, p.text, pos, end, st, rep, m, wfin + run0, dead);
         }
         for (uint32_t rb = 0; rb < (set_path ? 0u : total_runs); rb += 32) {
             bool my_pending;
@@ -1163,7 +1161,7 @@ DeviceScratch *scratch_for(const ridfa_program *P, int dev, size_t bytes, int *e
 }
 
 enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3, kModePart16 = 4, kModeFlat = 5,
-                       kModeRep16x4 = 6 };
+                       kModeRep16x4 = 6, kModeRep16x4C = 7 };
 
 // How one reach launch is laid out: table layout, text path, block/grid, shared memory.
 struct ReachPlan {
@@ -1188,8 +1186,9 @@ constexpr int block_cap2() { return R <= 4 ? 768 : 512; }
 template <int R, class LUT, int PATH>
 cudaError_t reach_one(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
     using KernT = void (*)(ReachArgs, int, uint32_t);
-    KernT kern = PATH == kPathCoop2 ? rid_reach2_kernel<R, LUT, block_cap2<R>()>
-                                    : rid_reach_kernel<R, LUT, block_cap<R, PATH>(), PATH == kPathCoop2 ? kPathGlobal : PATH>;
+    KernT kern;
+    if constexpr (PATH == kPathCoop2) kern = rid_reach2_kernel<R, LUT, block_cap2<R>()>;
+    else kern = rid_reach_kernel<R, LUT, block_cap<R, PATH>(), PATH>;
     if (pl.pslot) {
         if constexpr (R == 1 && (PATH == kPathGlobal || PATH == kPathCoop || PATH == kPathCoopSet))
             kern = rid_reach_kernel<1, LUT, block_cap<1, PATH>(), PATH, true>;
@@ -1220,6 +1219,10 @@ cudaError_t reach_m(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, in
         case kModeRep32: return reach_r<LutRep<false>, PATH>(a, pl, st, per_sm);
         case kModePart16: return reach_r<LutPart, PATH>(a, pl, st, per_sm);
         case kModeRep16x4: return reach_r<LutRep16x4, PATH>(a, pl, st, per_sm);
+        case kModeRep16x4C:
+            // (the compact class table serves the set path and plain global loads only)
+            if constexpr (PATH == kPathCoopSet || PATH == kPathGlobal) return reach_r<LutRep16x4C, PATH>(a, pl, st, per_sm);
+            else return cudaErrorInvalidValue;
         case kModePlain: return reach_r<LutPlain, PATH>(a, pl, st, per_sm);
         default: return reach_r<LutFlat, PATH>(a, pl, st, per_sm);
     }
@@ -1244,6 +1247,7 @@ cudaError_t piece_dispatch(const ReachArgs &a, const ReachPlan &pl, int sms, cud
         case kModeRep32: return piece_r<LutRep<false>>(pl.R, a, grid, smem, pl.tis, st);
         case kModePart16: return piece_r<LutPart>(pl.R, a, grid, smem, pl.tis, st);
         case kModeRep16x4: return piece_r<LutRep16x4>(pl.R, a, grid, smem, pl.tis, st);
+        case kModeRep16x4C: return piece_r<LutRep16x4C>(pl.R, a, grid, smem, pl.tis, st);
         case kModePlain: return piece_r<LutPlain>(pl.R, a, grid, smem, pl.tis, st);
         default: return piece_r<LutFlat>(pl.R, a, grid, smem, pl.tis, st);
     }
@@ -1288,10 +1292,12 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // (the half-replicated layout does not replace the compact one: on the codon RE it measured
     // slower -- its gathers conflict less, but its larger footprint leaves fewer warps and the
     // time goes to run imbalance, not conflicts)
-    const size_t plain = LutPlain::smem_bytes(A), flat = LutFlat::smem_bytes(A), rep16x4 = LutRep16x4::smem_bytes(A);
+    const size_t plain = LutPlain::smem_bytes(A), flat = LutFlat::smem_bytes(A), rep16x4 = LutRep16x4::smem_bytes(A),
+                 rep16x4c = LutRep16x4C::smem_bytes(A);
     const bool ok16 = LutRep<true>::fits16(A) && rep16 <= limit, ok32 = rep32 <= limit,
                okp = LutPart::fits(A) && part16 <= limit, okplain = LutPlain::fits(A) && plain <= limit,
-               ok16x4 = LutRep16x4::fits(A) && rep16x4 <= limit;
+               ok16x4 = LutRep16x4::fits(A) && rep16x4 <= limit,
+               ok16x4c = LutRep16x4C::fits(A) && rep16x4c + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit;
     // replicated layouts that leave room for at least 16 warps' staging come first; a 32-bit table
     // that leaves fewer is taken only when no scaled 16-bit one fits (measured: a 6-warp 32-bit
     // table ran at a third of the speed of a 26-warp scaled one)
@@ -1315,14 +1321,16 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
         }
     }
     if (mode == kModeRep16x4 && !ok16x4) return RIDFA_E_ARG;
+    if (mode == kModeRep16x4C && !ok16x4c) return RIDFA_E_ARG;
     if (mode == kModePlain && !okplain) mode = kModeFlat;    // the compact table, through generic loads
     if ((mode == kModeRep16 && !ok16) || (mode == kModeRep32 && !ok32) || (mode == kModePart16 && !okp))
         return RIDFA_E_ARG;
-    if (mode < kModePlain || mode > kModeRep16x4) return RIDFA_E_ARG;
+    if (mode < kModePlain || mode > kModeRep16x4C) return RIDFA_E_ARG;
     pl.mode = mode;
     pl.tis = (mode == kModeFlat && flat <= limit) ? 1 : 0;
     const size_t table_smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : mode == kModePart16 ? part16
-                              : mode == kModeRep16x4 ? rep16x4 : mode == kModePlain ? plain : (pl.tis ? flat : 256);
+                              : mode == kModeRep16x4 ? rep16x4 : mode == kModeRep16x4C ? rep16x4c
+                              : mode == kModePlain ? plain : (pl.tis ? flat : 256);
     const int cap = pl.R <= 4 ? 1024 : 512;
     const uint32_t text_path = tuning ? tuning->text_path : 0;
     if (text_path > 5) return RIDFA_E_ARG;
@@ -1347,7 +1355,7 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // Automata whose table is too large to replicate are the ones whose runs stay apart: there a
     // lane finishes all of its chunk's runs together (measured on the codon RE: 1.21x; on
     // replicated-table workloads the 512-thread cap of that variant cost 8-13%).
-    const bool many_runs = mode == kModePlain || mode == kModeFlat;
+    const bool many_runs = mode == kModePlain || mode == kModeFlat || mode == kModeRep16x4C;
     if (text_path == 0)
         pl.path = !aligned ? kPathGlobal
                   : !w_coop ? kPathGlobal
@@ -1360,11 +1368,23 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     if (pl.path == kPathCoop && !(aligned && w_coop)) return RIDFA_E_ARG;
     if (pl.path == kPathCoop2 && !(aligned && w_coop2)) return RIDFA_E_ARG;
     if (pl.path == kPathCoopSet && !(aligned && w_set)) return RIDFA_E_ARG;
+    // the compact class table is built for the set path (and plain global loads)
+    if (mode == kModeRep16x4C && pl.path != kPathCoopSet && pl.path != kPathGlobal) return RIDFA_E_ARG;
     const int warps_fit = pl.path == kPathCoop      ? w_coop
                           : pl.path == kPathCoopSet ? w_set
                           : pl.path == kPathCoop2 ? w_coop2
                                                   : cap / 32;
-    if (block == 0) block = pl.path == kPathGlobal ? (mode == kModeFlat && !pl.tis ? 256 : cap) : warps_fit * 32;
+    const uint64_t tasks = (static_cast<uint64_t>(ra.c) + (pl.path == kPathCoop2 ? 63 : 31)) /
+                           (pl.path == kPathCoop2 ? 64 : 32);
+    if (block == 0) {
+        block = pl.path == kPathGlobal ? (mode == kModeFlat && !pl.tis ? 256 : cap) : warps_fit * 32;
+        // fewer tasks than SMs x warps: spread them over every SM instead of filling some SMs'
+        // blocks and leaving the rest idle (at least 4 warps a block: each block loads the tables)
+        if (pl.path != kPathGlobal) {
+            const uint64_t per_sm_warps = std::max<uint64_t>(4, (tasks + sms - 1) / sms);
+            if (per_sm_warps < static_cast<uint64_t>(block / 32)) block = static_cast<int>(per_sm_warps) * 32;
+        }
+    }
     const int bcap = pl.path == kPathCoop2 ? cap2 : pl.path == kPathCoopSet ? 512 : cap;
     if (block < 32 || block > bcap || block % 32) return RIDFA_E_ARG;
     pl.block = block;
@@ -1372,8 +1392,6 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
                   ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpCoopBytes
               : pl.path == kPathCoop2 ? pl.staging_offset + static_cast<size_t>(block / 32) * kWarpCoop2Bytes
                                       : table_smem;
-    const uint64_t tasks = (static_cast<uint64_t>(ra.c) + (pl.path == kPathCoop2 ? 63 : 31)) /
-                           (pl.path == kPathCoop2 ? 64 : 32);
     if (tuning && tuning->grid_blocks) {
         pl.grid = static_cast<int>(tuning->grid_blocks);
     } else {

@@ -266,20 +266,32 @@ struct LutRep {
 // s' * Cp * 16 (the row offset over 4), so automata up to P * Cp <= 4095 fit the entries where
 // byte offsets would overflow them; a step is a shift-add of the state, an add of the class offset
 // and one ld.shared.u16.
-struct LutRep16x4 {
-    uint32_t lc, lt;          // shared addresses of this lane's class / transition copies
+// CC (compact classes): the class table is one copy of 256 16-bit class offsets (512 bytes)
+// instead of 32 lane copies (32 KB).  Byte b's entry sits in bank (b >> 1) & 31, so lanes reading
+// bytes of one 64-byte stretch (A, C, G, T; ASCII digits) never conflict and others at most
+// rarely; the 32 KB it saves go to staging, i.e. to more warps beside a large replicated table.
+template <bool CC>
+struct LutRep16x4T {
+    uint32_t lc, lt;          // shared addresses of this lane's class copy (CC: the one copy) /
+                              // transition copy
     uint32_t row4;            // 4-byte units per state row: Cp * 16
     __host__ __device__ static uint32_t cpad(const Automaton &A) { return (A.C + 1) & ~1u; }
-    static size_t smem_bytes(const Automaton &A) { return 256 * 128 + static_cast<size_t>(A.n + 1) * cpad(A) * 64; }
+    __host__ __device__ static constexpr size_t class_bytes() { return CC ? 512 : 256 * 128; }
+    static size_t smem_bytes(const Automaton &A) { return class_bytes() + static_cast<size_t>(A.n + 1) * cpad(A) * 64; }
     static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n) * cpad(A) * 16 <= 0xFFFF; }
     __device__ __forceinline__ static uint32_t cls_off(uint32_t c) { return (c >> 1) * 128 + (c & 1) * 2; }
     __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
         const uint32_t Cp = cpad(A);
         row4 = Cp * 16;
         const uint32_t base_c = smem_addr(smem);
-        const uint32_t base_t = base_c + 256 * 128;
-        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x)
-            sts_u32(base_c + i * 4, cls_off(A.classmap[i >> 5]));
+        const uint32_t base_t = base_c + static_cast<uint32_t>(class_bytes());
+        if (CC) {
+            for (uint32_t i = threadIdx.x; i < 128; i += blockDim.x)
+                sts_u32(base_c + i * 4, cls_off(A.classmap[2 * i]) | (cls_off(A.classmap[2 * i + 1]) << 16));
+        } else {
+            for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x)
+                sts_u32(base_c + i * 4, cls_off(A.classmap[i >> 5]));
+        }
         const uint32_t words = (A.n + 1) * Cp / 2;
         for (uint32_t i = threadIdx.x; i < words * 32; i += blockDim.x) {
             const uint32_t w = i >> 5;
@@ -289,15 +301,21 @@ struct LutRep16x4 {
             sts_u32(base_t + i * 4, (n0 * row4) | ((n1 * row4) << 16));
         }
         const uint32_t lane = threadIdx.x & 31;
-        lc = base_c + lane * 4;
+        lc = CC ? base_c : base_c + lane * 4;
         lt = base_t + lane * 4;
     }
     __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id * row4; }
     __device__ __forceinline__ uint32_t id(uint32_t s) const { return s / row4; }
-    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
-    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const {
+        return CC ? lds_u16(lc + b * 2) : lds_u32(lc + b * 128);
+    }
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const {
+        return CC ? lds_u16(lc + (byte_of(w, q) << 1)) : lds_u32(lc + (byte_of(w, q) << 7));
+    }
     __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return lds_u16(lt + (s << 2) + c); }
 };
+using LutRep16x4 = LutRep16x4T<false>;
+using LutRep16x4C = LutRep16x4T<true>;
 
 // Half-replicated tables, for transition tables too large to replicate 32 times: the class table
 // as in LutRep (32 copies, conflict-free), the transition table in F = 16 copies, lane l reading
@@ -629,14 +647,85 @@ __device__ __forceinline__ void coop_converge(const LUT &T, uint32_t stg_base, u
     __syncwarp();
 }
 
+// Runs of one lane on the set path: slots s[0..kMaxRun) hold states (dead where unused), and
+// `rep` maps each handed-off group g (4 bits at 4g) to the slot its run lives in, or 0xF once it
+// died.  compact_runs drops dead runs and runs in the same state as an earlier slot (they would
+// repeat its lookups from here on: the merging of Sec. 5's convergence, now inside the lane) and
+// packs the survivors into slots 0..cnt-1 in their order; it returns cnt.  Register arrays are
+// only indexed by compile-time constants (select networks), so nothing spills to local memory.
+__device__ __forceinline__ uint32_t compact_runs(uint32_t (&s)[kMaxRun], uint32_t &rep, uint32_t dead) {
+    uint32_t nidx = 0;        // 4 bits per old slot: its new slot, 0xF when dropped as dead
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxRun; ++j) {
+        uint32_t idx = 0xF;
+        if (s[j] != dead) {
+#pragma unroll
+            for (int i = 0; i < j; ++i)
+                if (idx == 0xF && s[i] == s[j]) idx = (nidx >> (4 * i)) & 0xF;
+            if (idx == 0xF) idx = cnt++;
+        }
+        nidx |= idx << (4 * j);
+    }
+    uint32_t t[kMaxRun];
+#pragma unroll
+    for (int k = 0; k < kMaxRun; ++k) t[k] = dead;
+#pragma unroll
+    for (int j = 0; j < kMaxRun; ++j) {
+        const uint32_t idx = (nidx >> (4 * j)) & 0xF;
+#pragma unroll
+        for (int k = 0; k < kMaxRun; ++k)
+            if (idx == static_cast<uint32_t>(k)) t[k] = s[j];     // a merged slot rewrites its leader's value
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxRun; ++k) s[k] = t[k];
+    uint32_t nrep = 0;
+#pragma unroll
+    for (int g = 0; g < kMaxRun; ++g) {
+        const uint32_t r = (rep >> (4 * g)) & 0xF;
+        nrep |= (r == 0xF ? 0xFu : (nidx >> (4 * r)) & 0xF) << (4 * g);
+    }
+    rep = nrep;
+    return cnt;
+}
+
+// One staged 64-byte window for the first M run slots of a lane (M is the same in the whole warp:
+// the largest live count; a lane's unused slots hold the dead state, which maps to itself).
+template <class LUT, int M>
+__device__ __forceinline__ void set_window(const LUT &T, uint32_t sb, uint32_t sw, uint32_t o0, uint32_t o1,
+                                           uint32_t (&s)[kMaxRun]) {
+    if (o0 == 0 && o1 == kCoopWin) {
+#pragma unroll
+        for (uint32_t q16 = 0; q16 < kCoopWin / 16; ++q16) {
+            const uint4 x = lds_v4(sb + 16 * (q16 ^ sw));
+            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+            uint32_t cl[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) cl[q] = T.cls_at(w[q >> 2], q & 3);
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+#pragma unroll
+                for (int g = 0; g < M; ++g) s[g] = T.next(s[g], cl[q]);
+        }
+    } else {
+        for (uint32_t o = o0; o < o1; ++o) {
+            const uint32_t c = T.cls_of(lds_u8(sb + 16 * ((o >> 4) ^ sw) + (o & 15)));
+#pragma unroll
+            for (int g = 0; g < M; ++g) s[g] = T.next(s[g], c);
+        }
+    }
+}
+
 // coop_converge for a lane that carries all the runs of one chunk together (up to kMaxRun states
 // handed off at one position): the text is staged once per chunk and each byte's class is looked
-// up once for all of them, so m runs cost 1 + m lookups per byte instead of 2m.  Dead states stay
-// dead (the dead row maps to itself) and are skipped once a whole granule has passed.
+// up once for all of them, so m runs cost 1 + m lookups per byte instead of 2m.  Every four
+// windows the lane's runs are compacted (dead runs dropped, runs that met merged) and the warp's
+// loop is respecialised to the largest live count M, so a byte costs 1 + M lookups and no
+// instruction is issued for a run that is gone.
 template <class LUT>
 __device__ __forceinline__ void coop_converge_set(const LUT &T, uint32_t stg_base, uint32_t lane, bool pending,
                                                   const uint8_t *base, uint64_t lim, uint64_t stop, uint64_t &pos,
-                                                  uint32_t (&s)[kMaxRun], uint32_t m, uint32_t dead) {
+                                                  uint32_t (&s)[kMaxRun], uint32_t &rep, uint32_t dead) {
     const uint64_t wb = pos & ~static_cast<uint64_t>(15);
     const uint32_t nwin = (pending && wb < stop)
                               ? static_cast<uint32_t>((stop - wb + kCoopWin - 1) / kCoopWin) : 0;
@@ -644,10 +733,8 @@ __device__ __forceinline__ void coop_converge_set(const LUT &T, uint32_t stg_bas
     const uint64_t wlim = reinterpret_cast<uint64_t>(base) + lim;
     const uint32_t g = lane & 3;
     const uint32_t max_win = __reduce_max_sync(kFull, nwin);
-    uint32_t live = 0;
-#pragma unroll
-    for (int q = 0; q < kMaxRun; ++q)
-        if (q < static_cast<int>(m) && s[q] != dead) live |= 1u << q;
+    uint32_t cnt = pending ? compact_runs(s, rep, dead) : 0;
+    uint32_t M = __reduce_max_sync(kFull, cnt);
     auto issue = [&](uint32_t r) {
         const uint32_t buf = stg_base + (r & 1) * kCoopBufBytes;
 #pragma unroll
@@ -660,11 +747,6 @@ __device__ __forceinline__ void coop_converge_set(const LUT &T, uint32_t stg_bas
         }
         cp_async_commit();
     };
-    auto step = [&](uint32_t c) {
-#pragma unroll
-        for (int q = 0; q < kMaxRun; ++q)
-            if (live & (1u << q)) s[q] = T.next(s[q], c);
-    };
     issue(0);
     const uint32_t sw = (lane >> 1) & 3;
     for (uint32_t r = 0; r < max_win; ++r) {
@@ -673,31 +755,27 @@ __device__ __forceinline__ void coop_converge_set(const LUT &T, uint32_t stg_bas
         cp_async_wait1();
         __syncwarp();
         const uint64_t ws = wb + static_cast<uint64_t>(kCoopWin) * r;
-        if (r < nwin && live) {
+        if (r < nwin && cnt) {
             const uint32_t sb = stg_base + (r & 1) * kCoopBufBytes + 64 * lane;
             const uint64_t lo = max(pos, ws), hi = min(stop, ws + kCoopWin);
-            if (lo == ws && hi == ws + kCoopWin) {
-#pragma unroll
-                for (uint32_t q16 = 0; q16 < kCoopWin / 16; ++q16) {
-                    const uint4 x = lds_v4(sb + 16 * (q16 ^ sw));
-                    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) step(T.cls_at(w[q >> 2], q & 3));
-                    uint32_t nl = 0;
-#pragma unroll
-                    for (int q = 0; q < kMaxRun; ++q)
-                        if ((live & (1u << q)) && s[q] != dead) nl |= 1u << q;
-                    live = nl;
-                }
-            } else {
-                for (uint64_t q = lo; q < hi; ++q) {
-                    const uint32_t o = static_cast<uint32_t>(q - ws);
-                    step(T.cls_of(lds_u8(sb + 16 * ((o >> 4) ^ sw) + (o & 15))));
-                }
+            const uint32_t o0 = static_cast<uint32_t>(lo - ws), o1 = static_cast<uint32_t>(hi - ws);
+            switch (M) {
+                case 1: set_window<LUT, 1>(T, sb, sw, o0, o1, s); break;
+                case 2: set_window<LUT, 2>(T, sb, sw, o0, o1, s); break;
+                case 3: set_window<LUT, 3>(T, sb, sw, o0, o1, s); break;
+                case 4: set_window<LUT, 4>(T, sb, sw, o0, o1, s); break;
+                case 5: set_window<LUT, 5>(T, sb, sw, o0, o1, s); break;
+                case 6: set_window<LUT, 6>(T, sb, sw, o0, o1, s); break;
+                case 7: set_window<LUT, 7>(T, sb, sw, o0, o1, s); break;
+                default: set_window<LUT, 8>(T, sb, sw, o0, o1, s); break;
             }
             pos = hi;
         }
         __syncwarp();
+        if ((r & 3) == 3) {
+            if (cnt) cnt = compact_runs(s, rep, dead);
+            M = __reduce_max_sync(kFull, cnt);
+        }
     }
     cp_async_wait0();
     __syncwarp();
@@ -727,6 +805,29 @@ __device__ __forceinline__ void tail_converge(const LUT &T, const uint8_t *t, ui
     while (pos < end && s != dead) {
         s = T.next(s, T.cls_of(__ldg(t + pos)));
         ++pos;
+    }
+}
+
+// After coop_converge_set: the runs' rest past the staged part (plain loads), then the final state
+// of each handed-off group g < m into fin[g] (the dead state when its run died).
+template <class LUT>
+__device__ __forceinline__ void finish_set_runs(const LUT &T, const uint8_t *text, uint64_t pos, uint64_t end,
+                                                uint32_t (&s)[kMaxRun], uint32_t rep, uint32_t m, uint32_t *fin,
+                                                uint32_t dead) {
+#pragma unroll
+    for (int k = 0; k < kMaxRun; ++k) {
+        uint64_t pk = pos;
+        tail_converge<LUT, false>(T, text, pk, end, s[k], dead);
+    }
+#pragma unroll
+    for (int gg = 0; gg < kMaxRun; ++gg) {
+        if (gg >= static_cast<int>(m)) continue;
+        const uint32_t r = (rep >> (4 * gg)) & 0xF;
+        uint32_t v = dead;
+#pragma unroll
+        for (int k = 0; k < kMaxRun; ++k)
+            if (r == static_cast<uint32_t>(k)) v = s[k];
+        fin[gg] = v;
     }
 }
 

@@ -452,3 +452,42 @@ def test_c3_4gib_bench_workload_sampled_rows():
     d[pos] = keep
     del d, maps, host
     torch.cuda.empty_cache()
+
+
+def test_compact_class_table_layout():
+    """Table layout 7: the lane-replicated transition table of layout 6 beside one 512-byte copy of
+    the class table, on the set path (aligned texts) and plain global loads (unaligned ones).
+    Every row equals the oracle's: the codon RE (runs stay apart: several runs per lane), record
+    lines, the regexp family, pieces (few chunks: lockstep pieces and look-back start sets);
+    the cooperative single-run paths refuse the layout."""
+    re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
+    x = textgen.c2_text((1 << 20) + 13, seed=201)
+    for c in (1000, 3001):
+        check(re2, x, c, dfa_too=False, rows=list(range(c)), tuning=dict(table_mode=7))
+    check(re2, x, 1000, dfa_too=False, rows=list(range(1000)), tuning=dict(table_mode=7, text_path=1))
+    y, _ = textgen.mutate(x, seed=202, n_subs=5, alphabet=b"ACGTN")
+    check(re2, y, 777, dfa_too=False, rows=list(range(777)), tuning=dict(table_mode=7))
+    check(re2, x, 2, dfa_too=False, tuning=dict(table_mode=7))          # look-back pieces
+    x3 = textgen.c3_text(1 << 18, seed=203)
+    for c in (1, 1000, 4099):
+        check(textgen.C3_RE, x3, c, tuning=dict(table_mode=7))
+    check(textgen.regexp_family_re(7), textgen.regexp_family_text(1 << 18, seed=204), 1000,
+          tuning=dict(table_mode=7))
+    x1 = textgen.c1_text(1 << 16, seed=205)
+    check(textgen.C1_RE, x1, 4, tuning=dict(table_mode=7))              # lockstep pieces
+    prog = lib.ridfa_compile(re2)
+    o, ser = oracle(re2)
+    base = torch.from_numpy(np.concatenate([np.zeros(16, np.uint8), x])).to("cuda:0")
+    d = base[16 + 3:]
+    z = x[3:]
+    maps = torch.empty((500, prog.info["k"]), dtype=torch.int16, device="cuda:0")
+    acc = lib.ridfa_recognize(prog, d, z.size, 500, tuning=dict(table_mode=7), d_chunk_maps=maps)
+    assert acc == ser.accepts(z)
+    got = maps.cpu().numpy().view(np.uint16)
+    want = o.lambda_rows(z, 500, [0, 1, 250, 498, 499])
+    for i in want:
+        assert np.array_equal(got[i], want[i])
+    for tp in (3, 4):
+        with pytest.raises(lib.RidfaError) as e:
+            lib.ridfa_recognize(prog, to_device(x), x.size, 1000, tuning=dict(table_mode=7, text_path=tp))
+        assert e.value.code == -1
