@@ -43,11 +43,11 @@ WORKLOADS = {
 REGEXP_K = 7   # (a|b)*a(a|b){7}: the minimal DFA has 256 states (the comparator's limit), k = 9
 
 
-def workload_re(name):
+def workload_re(name, k=REGEXP_K):
     import textgen
     return {"c3": textgen.C3_RE, "c3any": textgen.C3_RE_ANYFIELD,
             "c2": textgen.C2_RE.replace("{20,60}", "{2,4}"), "c1": textgen.C1_RE,
-            "regexp": textgen.regexp_family_re(REGEXP_K)}[name]
+            "regexp": textgen.regexp_family_re(k)}[name]
 
 
 def make_text(name, n, seed, device):
@@ -237,7 +237,7 @@ def run_reference(args, rank):
     if name in ("batch", "served"):
         run_reference_multi(args, name)
         return
-    re_src = workload_re(name)
+    re_src = workload_re(name, args.k)
     from oracle.recognizer import SerialRecognizer
     ser = SerialRecognizer(re_src)
     per_step = 16 << 20
@@ -572,6 +572,8 @@ def main():
     ap.add_argument("--text-bytes", type=int, default=None)
     ap.add_argument("--chunks", type=int, default=None)
     ap.add_argument("--seed", type=int, default=0x5EED02)
+    ap.add_argument("--k", type=int, default=REGEXP_K,
+                    help="--workload regexp: the k of (a|b)*a(a|b){k} (the paper's regexp family)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dfa", action="store_true")
@@ -619,7 +621,7 @@ def main():
     desc, n_default, c_default = WORKLOADS[name]
     n_req = args.text_bytes or n_default
     c = args.chunks or c_default
-    re_src = workload_re(name)
+    re_src = workload_re(name, args.k)
     prog = lib.ridfa_compile(re_src)
     info = prog.info
     d_text = make_text(name, n_req, args.seed + rank, dev)

@@ -312,12 +312,18 @@ typedef struct {
 } ridfa_batch_item;
 
 typedef struct {
-    uint32_t chunk_len;      /* bytes per chunk for items with n_chunks == 0; 0 = autotune: the
-                                length is looked up in a cache keyed by every program's
-                                (log2 |P|, log2 k, log2 C), else candidate lengths are timed on
-                                this batch and the winner is cached under those keys */
+    uint32_t chunk_len;      /* bytes per chunk for items with n_chunks == 0; 0 = autotune: chunk
+                                length and launch shape are looked up in a cache keyed by every
+                                program's (log2 |P|, log2 k, log2 C), else timed on this batch --
+                                chunk lengths 4-32 KiB, then warps per block (all that fit, 16,
+                                8), then the run interleave below -- and the winner is cached
+                                under those keys */
     uint32_t no_graph;       /* 1: run() enqueues the launches directly instead of a CUDA graph */
-    uint32_t reserved[2];
+    uint32_t block_warps;    /* warps per block of the reach launches at most (threads per task
+                                group); 0 = as many as fit (tuned when chunk_len == 0); <= 32 */
+    uint32_t set_mode;       /* tables too large to replicate (runs that stay apart): 1 a lane
+                                carries all of its chunk's runs, interleaved, through one pass; 2
+                                one run per lane; 0 = 1 (tuned when chunk_len == 0) */
 } ridfa_batch_opts;
 
 typedef struct {
@@ -325,6 +331,8 @@ typedef struct {
     uint64_t total_chunks;
     uint32_t n_programs, n_launches, n_tasks, n_segments;
     uint32_t chunk_len;      /* the chunk length in use */
+    uint32_t block_warps;    /* warps per block cap in use (0: as many as fit) */
+    uint32_t set_mode;       /* run interleave in use (0/1 set path, 2 one run per lane) */
     uint32_t graph;          /* 1 if run() launches a CUDA graph */
     uint64_t device_bytes;   /* device memory the batch holds (descriptors, maps, summaries) */
 } ridfa_batch_stats;

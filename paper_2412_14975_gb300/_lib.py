@@ -304,13 +304,13 @@ class BatchItem(_c.Structure):
 
 
 class BatchOpts(_c.Structure):
-    _fields_ = [("chunk_len", _u32), ("no_graph", _u32), ("reserved", _u32 * 2)]
+    _fields_ = [("chunk_len", _u32), ("no_graph", _u32), ("block_warps", _u32), ("set_mode", _u32)]
 
 
 class BatchStats(_c.Structure):
     _fields_ = [("total_bytes", _c.c_uint64), ("total_chunks", _c.c_uint64), ("n_programs", _u32),
                 ("n_launches", _u32), ("n_tasks", _u32), ("n_segments", _u32), ("chunk_len", _u32),
-                ("graph", _u32), ("device_bytes", _c.c_uint64)]
+                ("block_warps", _u32), ("set_mode", _u32), ("graph", _u32), ("device_bytes", _c.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -357,10 +357,10 @@ class Batch:
         return self.handle
 
 
-def ridfa_batch_create(progs, items, d_accept, chunk_len=0, no_graph=False):
+def ridfa_batch_create(progs, items, d_accept, chunk_len=0, no_graph=False, block_warps=0, set_mode=0):
     """items: list of (device text, length, program index, n_chunks or 0)."""
     parr, iarr = _batch_arrays(progs, items)
-    opts = BatchOpts(int(chunk_len), int(bool(no_graph)), (_u32 * 2)(0, 0))
+    opts = BatchOpts(int(chunk_len), int(bool(no_graph)), int(block_warps), int(set_mode))
     h = _vp()
     _check(_lib.ridfa_batch_create(parr, len(progs), iarr, len(items), _ptr(d_accept), _c.byref(opts),
                                    _c.byref(h)), "ridfa_batch_create")

@@ -536,8 +536,16 @@ int blocks_per_sm(int device, const LaunchGroup &g, int *per_sm) {
 
 inline size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+// What the batch autotuner found for a batch: chunk length and launch shape.
+struct BatchTune {
+    uint32_t chunk_len = 0;
+    BatchShape shape;
+    bool operator==(const BatchTune &o) const {
+        return chunk_len == o.chunk_len && shape.warps_cap == o.shape.warps_cap && shape.set_mode == o.shape.set_mode;
+    }
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, uint32_t> g_tune_cache;   // (log2 |P|, log2 k, log2 C) -> chunk length
+std::map<std::tuple<int, int, int>, BatchTune> g_tune_cache;   // (log2 |P|, log2 k, log2 C) -> tune
 
 int log2i(uint32_t v) {
     int r = 0;
@@ -581,7 +589,7 @@ PlanStats plan_stats(const BatchPlan *pl) {
 }
 
 int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, const ridfa_batch_item *items,
-               uint32_t ni, uint32_t L, int device) {
+               uint32_t ni, uint32_t L, int device, const BatchShape &shape) {
     if (!pl || !progs || !np || (ni && !items) || L == 0) return RIDFA_E_ARG;
     for (uint32_t p = 0; p < np; ++p)
         if (!progs[p] || progs[p]->rid.k > RIDFA_MAX_SLOTS) return progs[p] ? RIDFA_E_UNSUPPORTED : RIDFA_E_ARG;
@@ -658,7 +666,7 @@ int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, co
         g.mode = m;
         // staged text when every text is 16-byte aligned; tables too large to replicate (their
         // runs stay apart) finish a chunk's runs together, at up to 512 threads
-        g.tp = !aligned_all ? kTpGlobal : (m == kBPlain || m == kBFlat) ? kTpSet : kTpCoop;
+        g.tp = !aligned_all ? kTpGlobal : (m == kBPlain || m == kBFlat) && shape.set_mode != 2 ? kTpSet : kTpCoop;
         for (uint32_t p = 0; p < np; ++p)
             if (mode[p] == m && prog_chunks[p]) {
                 g.progs.push_back(p);
@@ -671,6 +679,7 @@ int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t np, co
         const int cap = g.R <= 4 && g.tp != kTpSet ? 1024 : 512;
         g.stg = static_cast<uint32_t>((g.table_smem + 127) & ~static_cast<size_t>(127));
         int warps = g.tp != kTpGlobal ? static_cast<int>(std::min<size_t>(cap / 32, (limit - g.stg) / kWarpCoopBytes)) : cap / 32;
+        if (shape.warps_cap) warps = std::min<int>(warps, static_cast<int>(shape.warps_cap));
         warps = std::max(warps, 1);
         g.block = warps * 32;
         g.smem = g.tp != kTpGlobal ? g.stg + static_cast<size_t>(warps) * kWarpCoopBytes : g.table_smem;
@@ -829,6 +838,7 @@ struct ridfa_batch {
     std::vector<ridfa_batch_item> items;
     uint8_t *d_accept = nullptr;
     uint32_t chunk_len = 0;
+    ridfa::BatchShape shape;
     bool use_graph = true;
     ridfa::BatchPlan *plan = nullptr;
     void *dmem = nullptr;
@@ -857,7 +867,7 @@ int batch_build(ridfa_batch *B, uint32_t L) {
     if (!B->plan) B->plan = plan_new();
     if (!B->plan) return RIDFA_E_NOMEM;
     int err = plan_build(B->plan, B->progs.data(), static_cast<uint32_t>(B->progs.size()), B->items.data(),
-                         static_cast<uint32_t>(B->items.size()), L, B->device);
+                         static_cast<uint32_t>(B->items.size()), L, B->device, B->shape);
     if (err != RIDFA_OK) return err;
     const size_t total = plan_device_bytes(B->plan);
     cudaError_t e = cudaMalloc(&B->dmem, total);
@@ -900,33 +910,42 @@ int batch_run(ridfa_batch *B, cudaStream_t st) {
     return plan_enqueue(B->plan, static_cast<uint8_t *>(B->dmem), B->d_accept, st, true, &B->fork);
 }
 
-// Chunk length for the batch.  Every program is keyed by (log2 |P|, log2 k, log2 C); when all
-// keys are in the cache and agree, that length is used.  Otherwise candidate lengths are timed
-// on the batch itself (3 replays each, CUDA events) and the winner is recorded under every key.
-int batch_autotune(ridfa_batch *B, uint32_t *out_len) {
+// Chunk length and launch shape for the batch.  Every program is keyed by (log2 |P|, log2 k,
+// log2 C); when all keys are in the cache and agree, that tune is used.  Otherwise the batch itself
+// is timed (one warm-up and 3 replays per candidate, CUDA events), one knob after another: the
+// chunk length (4-32 KiB), then the warps per block of the reach groups (as many as fit, 16, 8),
+// then -- when some table is too large to replicate -- whether a lane finishes all of its chunk's
+// runs together or one run per lane.  The winner is recorded under every key.  Knobs the caller
+// fixed (opts->block_warps, opts->set_mode) are not searched.
+int batch_autotune(ridfa_batch *B, bool fixed_warps, bool fixed_set, BatchTune *out) {
     std::vector<std::tuple<int, int, int>> keys;
-    for (const ridfa_program *P : B->progs)
+    bool large_table = false;
+    for (const ridfa_program *P : B->progs) {
         keys.emplace_back(log2i(P->rid.n_states), log2i(P->rid.k), log2i(P->rid.n_classes));
+        const HostAutomaton &H = P->rid;
+        Automaton A{nullptr, nullptr, nullptr, nullptr, nullptr, H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+        if (!LutRep<true>::fits16(A) && !LutRep16x4::fits(A)) large_table = true;
+    }
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        uint32_t v = 0;
-        bool all = true;
+        BatchTune v;
+        bool all = true, first = true;
         for (auto &k : keys) {
             auto it = g_tune_cache.find(k);
-            if (it == g_tune_cache.end() || (v && it->second != v)) {
+            if (it == g_tune_cache.end() || (!first && !(it->second == v))) {
                 all = false;
                 break;
             }
             v = it->second;
+            first = false;
         }
-        if (all && v) {
-            *out_len = v;
+        if (all && v.chunk_len) {
+            if (fixed_warps) v.shape.warps_cap = B->shape.warps_cap;
+            if (fixed_set) v.shape.set_mode = B->shape.set_mode;
+            *out = v;
             return RIDFA_OK;
         }
     }
-    const uint32_t cands[] = {4096, 8192, 16384, 32768};
-    float best = 1e30f;
-    uint32_t best_len = 8192;
     cudaStream_t st;
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -934,9 +953,14 @@ int batch_autotune(ridfa_batch *B, uint32_t *out_len) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     int err = RIDFA_OK;
-    for (uint32_t L : cands) {
-        err = batch_build(B, L);
-        if (err != RIDFA_OK) break;
+    BatchTune best;
+    best.chunk_len = 8192;
+    best.shape = B->shape;
+    float best_ms = 1e30f;
+    auto trial = [&](const BatchTune &t) {
+        B->shape = t.shape;
+        err = batch_build(B, t.chunk_len);
+        if (err != RIDFA_OK) return;
         batch_run(B, st);                       // warm-up
         cudaEventRecord(a, st);
         for (int r = 0; r < 3; ++r) batch_run(B, st);
@@ -944,14 +968,32 @@ int batch_autotune(ridfa_batch *B, uint32_t *out_len) {
         e = cudaEventSynchronize(b);
         if (e != cudaSuccess) {
             err = cuda_fail(e);
-            break;
+            return;
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, a, b);
-        if (ms < best) {
-            best = ms;
-            best_len = L;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
         }
+    };
+    for (uint32_t L : {4096u, 8192u, 16384u, 32768u}) {
+        if (err != RIDFA_OK) break;
+        BatchTune t = best;
+        t.chunk_len = L;
+        trial(t);
+    }
+    if (!fixed_warps)
+        for (uint32_t w : {16u, 8u}) {
+            if (err != RIDFA_OK) break;
+            BatchTune t = best;
+            t.shape.warps_cap = w;
+            trial(t);
+        }
+    if (!fixed_set && large_table && err == RIDFA_OK) {
+        BatchTune t = best;
+        t.shape.set_mode = best.shape.set_mode == 2 ? 1 : 2;
+        trial(t);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -959,9 +1001,9 @@ int batch_autotune(ridfa_batch *B, uint32_t *out_len) {
     if (err != RIDFA_OK) return err;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        for (auto &k : keys) g_tune_cache[k] = best_len;
+        for (auto &k : keys) g_tune_cache[k] = best;
     }
-    *out_len = best_len;
+    *out = best;
     return RIDFA_OK;
 }
 
@@ -993,8 +1035,21 @@ extern "C" int ridfa_batch_create(const ridfa_program *const *progs, uint32_t n_
     B->d_accept = d_accept;
     B->use_graph = !(opts && opts->no_graph);
     uint32_t L = opts ? opts->chunk_len : 0;
+    B->shape.warps_cap = opts ? opts->block_warps : 0;
+    B->shape.set_mode = opts ? opts->set_mode : 0;
+    if (B->shape.warps_cap > 32 || B->shape.set_mode > 2) {
+        delete B;
+        return RIDFA_E_ARG;
+    }
     int err = ridfa::make_fork(&B->fork);
-    if (err == RIDFA_OK && L == 0) err = ridfa::batch_autotune(B, &L);
+    if (err == RIDFA_OK && L == 0) {
+        ridfa::BatchTune t;
+        err = ridfa::batch_autotune(B, B->shape.warps_cap != 0, B->shape.set_mode != 0, &t);
+        if (err == RIDFA_OK) {
+            L = t.chunk_len;
+            B->shape = t.shape;
+        }
+    }
     if (err == RIDFA_OK) err = ridfa::batch_build(B, L);
     if (err != RIDFA_OK) {
         ridfa::batch_release(B);
@@ -1025,6 +1080,8 @@ extern "C" int ridfa_batch_get_stats(const ridfa_batch *b, ridfa_batch_stats *ou
     out->n_tasks = s.n_tasks;
     out->n_segments = s.n_segments;
     out->chunk_len = b->chunk_len;
+    out->block_warps = b->shape.warps_cap;
+    out->set_mode = b->shape.set_mode;
     out->graph = b->exec ? 1 : 0;
     out->device_bytes = b->dbytes;
     return RIDFA_OK;
@@ -1047,7 +1104,7 @@ extern "C" void ridfa_batch_free(ridfa_batch *b) {
 extern "C" int ridfa_recognize_batch(const ridfa_program *const *progs, uint32_t n_progs,
                                      const ridfa_batch_item *items, uint32_t n_items, uint8_t *d_accept,
                                      void *stream) {
-    ridfa_batch_opts o{8192, 1, {0, 0}};   // one run: no graph
+    ridfa_batch_opts o{8192, 1, 0, 0};   // one run: no graph
     ridfa_batch *b = nullptr;
     int err = ridfa_batch_create(progs, n_progs, items, n_items, d_accept, &o, &b);
     if (err != RIDFA_OK) return err;

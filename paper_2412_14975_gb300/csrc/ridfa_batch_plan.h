@@ -22,11 +22,19 @@ struct BatchPlan;
 BatchPlan *plan_new();
 void plan_delete(BatchPlan *pl);
 
+// Launch shape of the reach groups (the batch autotuner's knobs besides the chunk length).
+struct BatchShape {
+    uint32_t warps_cap = 0;   // warps per block at most (0: as many as the staging buffers allow)
+    uint32_t set_mode = 0;    // tables too large to replicate: 0/1 a lane finishes all of its chunk's
+                              // runs together (the set path), 2 one run per lane
+};
+
 // Plan items[0..n_items) over progs[0..n_progs) on `device` (the current device), items with
 // n_chunks == 0 getting ceil(len / chunk_len) chunks.  Uploads program tables if needed.
 // Errors: E_ARG, E_CHUNKS, E_UNSUPPORTED, E_NOMEM, E_CUDA.
 int plan_build(BatchPlan *pl, const ridfa_program *const *progs, uint32_t n_progs,
-               const ridfa_batch_item *items, uint32_t n_items, uint32_t chunk_len, int device);
+               const ridfa_batch_item *items, uint32_t n_items, uint32_t chunk_len, int device,
+               const BatchShape &shape = BatchShape{});
 
 size_t plan_device_bytes(const BatchPlan *pl);   // whole device block
 size_t plan_image_bytes(const BatchPlan *pl);    // leading part written from the host image

@@ -192,3 +192,44 @@ def test_batch_compact_table_reading_frame(aligned):
         torch.cuda.synchronize()
         assert np.array_equal(acc.cpu().numpy().astype(bool), want), chunk_len
         b.close()
+
+
+def test_batch_launch_shapes_agree_and_autotune():
+    """The batch autotuner's knobs -- warps per block of the reach launches and, for tables too
+    large to replicate, a lane carrying all of its chunk's runs together or one run per lane --
+    give the same accept bits as the oracle in every combination; an autotuned batch reports the
+    shape it chose, and a second batch over the same programs reuses the cached tune."""
+    progs = [lib.ridfa_compile(r) for r in RES]
+    d, texts, items = build_items(51, 90, True, max_len=120_000)
+    want = expected(texts, items)
+    acc = torch.zeros(len(items), dtype=torch.uint8, device="cuda:0")
+    for warps in (0, 4, 8, 16):
+        for set_mode in (0, 1, 2):
+            acc.fill_(7)
+            b = lib.ridfa_batch_create(progs, items, acc, chunk_len=2048, block_warps=warps, set_mode=set_mode)
+            st = lib.ridfa_batch_get_stats(b)
+            assert st["block_warps"] == warps and st["set_mode"] == set_mode
+            lib.ridfa_batch_run(b)
+            torch.cuda.synchronize()
+            assert np.array_equal(acc.cpu().numpy().astype(bool), want), (warps, set_mode)
+            b.close()
+    acc.fill_(7)
+    b = lib.ridfa_batch_create(progs, items, acc, chunk_len=0)
+    st = lib.ridfa_batch_get_stats(b)
+    assert st["chunk_len"] in (4096, 8192, 16384, 32768)
+    assert st["block_warps"] in (0, 8, 16) and st["set_mode"] in (0, 1, 2)
+    lib.ridfa_batch_run(b)
+    torch.cuda.synchronize()
+    assert np.array_equal(acc.cpu().numpy().astype(bool), want)
+    b.close()
+    acc.fill_(7)
+    b2 = lib.ridfa_batch_create(progs, items[: len(items) // 2], acc, chunk_len=0)
+    st2 = lib.ridfa_batch_get_stats(b2)
+    assert (st2["chunk_len"], st2["block_warps"], st2["set_mode"]) == (st["chunk_len"], st["block_warps"], st["set_mode"])
+    lib.ridfa_batch_run(b2)
+    torch.cuda.synchronize()
+    assert np.array_equal(acc.cpu().numpy()[: len(items) // 2].astype(bool), want[: len(items) // 2])
+    b2.close()
+    with pytest.raises(lib.RidfaError) as e:
+        lib.ridfa_batch_create(progs, items, acc, chunk_len=2048, set_mode=3)
+    assert e.value.code == -1
