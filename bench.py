@@ -584,6 +584,8 @@ def main():
                     help="reach-kernel table layout (0 auto, 1 compact, 2 rep16, 3 rep32)")
     ap.add_argument("--piece-len", type=int, default=0,
                     help="intra-chunk speculation piece length (0 auto, 1 off, >= 64 bytes)")
+    ap.add_argument("--probe", type=int, default=0,
+                    help="bytes between convergence checks of the speculative runs (0 auto)")
     ap.add_argument("--text-path", type=int, default=0,
                     help="converged-phase text reads (0 auto, 1 global loads, 3 cooperative staging, 4 two chunks per lane, 5 set path)")
     args = ap.parse_args()
@@ -679,7 +681,8 @@ def main():
     # correctness guard of the timed configuration (device result vs the synchronous API)
     acc = lib.ridfa_recognize(prog, d_text, n, c, stream=stream)
 
-    tuning = {"table_mode": args.table_mode, "text_path": args.text_path, "piece_len": args.piece_len}
+    tuning = {"table_mode": args.table_mode, "text_path": args.text_path, "piece_len": args.piece_len,
+              "probe_interval": args.probe}
 
     def step_rid():
         lib.ridfa_recognize_async(prog, d_text, n, c, d_accept, tuning=tuning, stream=stream)
@@ -702,7 +705,8 @@ def main():
     for _ in range(5):
         lib.ridfa_recognize_async(prog, d_text, n, c, d_accept,
                                   tuning={"profile": 1, "table_mode": args.table_mode,
-                                          "text_path": args.text_path, "piece_len": args.piece_len}, stream=stream)
+                                          "text_path": args.text_path, "piece_len": args.piece_len,
+                                          "probe_interval": args.probe}, stream=stream)
         r, j = lib.ridfa_last_timings(prog)
         reach.append(r)
         joins.append(j)

@@ -105,7 +105,11 @@ typedef struct {
                                  6 lane-replicated 16-bit entries in 4-byte units (tables up to
                                  4x larger than mode 2 allows); 7 as 6 with one 512-byte copy of
                                  the class table (32 KB more for staging; text paths 1 and 5
-                                 only) (E_ARG if the chosen layout does not fit) */
+                                 only); 8 two-byte steps: lane-replicated 16-bit entries for every
+                                 pair of classes beside the single classes, so the converged runs
+                                 take one transition lookup per two bytes (small automata:
+                                 (P/2 + 1) * (C*C + C) <= 511; text paths 1 and 3 only) (E_ARG if
+                                 the chosen layout does not fit) */
     uint32_t text_path;       /* how the converged runs read the text: 0 auto; 1 each lane's own
                                  16-byte global loads; 2 retired (per-lane bulk copies; E_ARG);
                                  3 warp-cooperative coalesced loads staged in shared memory; 4

@@ -164,9 +164,9 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_batch_kernel(BatchReachArg
                 const uint64_t beg = chunk_begin(i, td->len, td->c), end = chunk_begin(i + 1, td->len, td->c);
                 uint64_t hp = 0;
                 uint32_t d, al[R];
-                const int m = speculate<R, LUT>(T, A, td->text, beg, end, b.probe, lane, start_state, start_live,
-                                                dead, P.maps + ch * A.k, P.dinfo + ch, b.status, true, false, &hp,
-                                                &d, al);
+                const int m = speculate<R, LUT, TP == kTpSet ? kMultiMinSet : kMultiMin>(
+                    T, A, td->text, beg, end, b.probe, lane, start_state, start_live, dead, P.maps + ch * A.k,
+                    P.dinfo + ch, b.status, true, false, &hp, &d, al);
                 if (m >= 1) {
                     handed |= 1u << j;
 #pragma unroll

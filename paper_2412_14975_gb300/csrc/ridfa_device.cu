@@ -34,7 +34,7 @@
 #include <vector>
 
 #include "ridfa_internal.h"
-#include "ridfa_kernels.cuh"
+#include "ridfa_reach.cuh"
 
 namespace ridfa {
 // --------------------------------------------------------------------------- host side
@@ -110,372 +110,6 @@ int smem_optin_limit() {
 
 
 namespace {
-
-template <int R, class LUT, int BLOCK, int PATH, bool PSLOT = false>
-__global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int table_in_smem,
-                                                            uint32_t staging_offset) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    const Automaton &A = p.A;
-    LUT T;
-    T.setup(A, smem, table_in_smem != 0);
-    // per-warp staging buffers of the cooperative text paths
-    const uint32_t warp_in_block = threadIdx.x >> 5;
-    const uint32_t stg_base = smem_addr(smem) + staging_offset + warp_in_block * kWarpCoopBytes;
-    __syncthreads();
-
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t dead = T.enc(A.n);
-    const uint64_t n_tasks = (static_cast<uint64_t>(p.c) + 31) / 32;
-    const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-    RunEntry *wruns = p.runs ? p.runs + warp0 * kRunsPerWarp : nullptr;
-    uint32_t *wfin = p.finals ? p.finals + warp0 * kFinalsPerWarp : nullptr;   // null with wruns
-    uint32_t *wball = wfin ? wfin + kRunsPerWarp : nullptr;
-
-    // slot start states of this lane (slot a = r*32 + lane)
-    static_assert(!PSLOT || R == 1, "per-chunk start states take one register");
-    uint32_t start_state[R];
-    uint32_t start_live = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t a = r * 32 + lane;
-        start_state[r] = (!PSLOT && a < A.k) ? T.enc(A.slot_state[a]) : dead;
-        if (!PSLOT && r * 32 < static_cast<int>(A.k)) start_live |= 1u << r;
-    }
-
-    for (uint64_t task = warp0; task < n_tasks; task += n_warps) {
-        const uint64_t chunk0 = task * 32;
-        // ---------------- speculative phase, one chunk at a time, lanes = runs
-        // A chunk whose live runs reduce to m <= kMaxRun distinct states hands them off as m
-        // runs; without a run list (no scratch) only m = 1, kept by lane j.
-        uint32_t my_hand = 0;         // owner lane j of a handed-off chunk: (m << 16) | first run
-        uint32_t nruns = 0, handed = 0;
-        uint32_t amask[R];            // bit j: this lane's slot of register r alive at chunk j's hand-off
-#pragma unroll
-        for (int r = 0; r < R; ++r) amask[r] = 0;
-        uint64_t one_pos = 0;
-        uint32_t one_state = dead;
-        for (uint32_t j = 0; j < 32; ++j) {
-            const uint64_t ch = chunk0 + j;
-            if (ch >= p.c) break;
-            const uint64_t beg = chunk_begin(ch, p.len, p.c);
-            const uint64_t end = chunk_begin(ch + 1, p.len, p.c);
-            if constexpr (PSLOT) {
-                // this chunk's own start states (one register: at most 32)
-                const uint32_t v = p.piece_slots[ch * 32 + lane];
-                start_state[0] = v < A.n ? T.enc(v) : dead;
-                start_live = __any_sync(kFull, start_state[0] != dead) ? 1u : 0u;
-            }
-            uint32_t d, alive[R];
-            uint64_t hp = 0;
-            const int m = speculate<R, LUT>(T, A, p.text, beg, end, p.probe, lane, start_state, start_live, dead,
-                                            p.maps + ch * p.stride, p.dinfo + ch, p.status, wruns != nullptr,
-                                            wruns == nullptr, &hp, &d, alive);
-            if (m >= 1) {
-                handed |= 1u << j;
-#pragma unroll
-                for (int r = 0; r < R; ++r) amask[r] |= ((alive[r] >> lane) & 1u) << j;
-                if (wruns) {
-                    if (lane < static_cast<uint32_t>(m))
-                        wruns[nruns + lane] = RunEntry{hp, d, static_cast<uint16_t>(j), static_cast<uint16_t>(lane)};
-                    if (lane == j) {
-                        my_hand = (static_cast<uint32_t>(m) << 16) | nruns;
-                    }
-                    nruns += static_cast<uint32_t>(m);
-                } else if (lane == j) {
-                    my_hand = (1u << 16) | j;
-                    one_pos = hp;
-                    one_state = d;
-                }
-            }
-        }
-        // the alive bits wait in the finals area while the runs go on (registers are scarce
-        // there); without it the rows carry tags instead
-        if (wball) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) wball[r * 32 + lane] = amask[r];
-        }
-        __syncwarp();
-
-        // ---------------- converged phase: each lane finishes one run (rounds of 32 runs); when
-        // some chunk handed off several runs (staged path), each lane finishes its chunk's runs
-        // together instead
-        const uint32_t total_runs = wruns ? nruns : 32;
-        uint32_t fin_reg = dead;      // final state of run `lane` when there are at most 32 runs
-        const bool set_path = PATH == kPathCoopSet && wruns && nruns != static_cast<uint32_t>(__popc(handed));
-        if (set_path) {
-            const uint32_t m = my_hand >> 16, run0 = my_hand & 0xFFFF;
-            uint32_t st[kMaxRun];
-            uint64_t pos = 0, end = 0;
-#pragma unroll
-            for (int g = 0; g < kMaxRun; ++g) st[g] = dead;
-            if (m) {
-#pragma unroll
-                for (int g = 0; g < kMaxRun; ++g)
-                    if (g < static_cast<int>(m)) st[g] = wruns[run0 + g].state;
-                pos = wruns[run0].pos;
-                end = chunk_begin(chunk0 + lane + 1, p.len, p.c);
-            }
-            const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
-            uint32_t rep = 0xFFFFFFFFu;                // group g -> its slot (4 bits; 0xF dead)
-#pragma unroll
-            for (int g = 0; g < kMaxRun; ++g)
-                if (g < static_cast<int>(m)) rep = (rep & ~(0xFu << (4 * g))) | (static_cast<uint32_t>(g) << (4 * g));
-            coop_converge_set(T, stg_base, lane, m != 0, p.text, lim, min(end, lim), pos, st, rep, dead);
-            if (m) finish_set_runs(T, p.text, pos, end, st, rep, m, wfin + run0, dead);
-        }
-        for (uint32_t rb = 0; rb < (set_path ? 0u : total_runs); rb += 32) {
-            bool my_pending;
-            uint64_t pos = 0, end = 0;
-            uint32_t s = dead, jj = lane;
-            const uint32_t idx = rb + lane;
-            if (wruns) {
-                my_pending = idx < nruns;
-                if (my_pending) {
-                    const RunEntry e = wruns[idx];
-                    pos = e.pos;
-                    s = e.state;
-                    jj = e.chunk;
-                }
-            } else {
-                my_pending = my_hand != 0;
-                pos = one_pos;
-                s = one_state;
-            }
-            if (my_pending) end = chunk_begin(chunk0 + jj + 1, p.len, p.c);
-            if ((PATH == kPathCoop || PATH == kPathCoopSet) && __any_sync(kFull, my_pending)) {
-                const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
-                coop_converge<LUT, true>(T, stg_base, lane, my_pending, p.text, lim, min(end, lim), pos, s, dead);
-            }
-            if (my_pending) {
-                tail_converge<LUT, PATH == kPathGlobal>(T, p.text, pos, end, s, dead);
-                if (total_runs > 32) wfin[idx] = s;
-                else fin_reg = s;
-            }
-        }
-        __syncwarp();
-        // ---------------- rows of the handed-off chunks, one chunk at a time by the warp
-        if (wball) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) amask[r] = wball[r * 32 + lane];
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) amask[r] = 0xFFFFFFFFu;    // tags decide
-        }
-        for (uint32_t hm = handed; hm; hm &= hm - 1) {
-            const uint32_t j = __ffs(hm) - 1;
-            const uint32_t hand = __shfl_sync(kFull, my_hand, j);
-            const uint32_t m = hand >> 16, run0 = hand & 0xFFFF;
-            const uint32_t src = run0 + min(lane, m - 1);     // lane g < m: run of group g
-            uint32_t fin = __shfl_sync(kFull, fin_reg, src & 31);
-            if (total_runs > 32 || set_path) fin = wfin[src];
-            uint32_t am = 0;
-#pragma unroll
-            for (int r = 0; r < R; ++r) am |= ((amask[r] >> j) & 1u) << r;
-            finish_handed_row<R, LUT>(T, p.maps + (chunk0 + j) * p.stride, A.k, m, m >= 2 || !wball, lane, am, fin,
-                                      dead, p.dinfo + chunk0 + j);
-        }
-    }
-}
-
-// ------------------------------------------------------------------ reach, two chains per lane
-// Speculative phase of one chunk by the whole warp (lanes = runs).  Returns true when the live
-// runs merged into one state before the chunk end; then *out_pos / *out_state hold where and
-// what, and alive[] the ballots of the slots still alive (the same in every lane).  Otherwise the
-// chunk finished here: its map row and D_i summary are written and false is returned.
-template <int R, class LUT>
-__device__ __forceinline__ bool speculate_chunk(const ReachArgs &p, const LUT &T, uint64_t ch,
-                                                uint32_t lane, const uint32_t (&start_state)[R],
-                                                uint32_t start_live, uint32_t dead, uint64_t *out_pos,
-                                                uint32_t *out_state, uint32_t (&alive)[R]) {
-    return speculate_range<R, LUT>(T, p.A, p.text, chunk_begin(ch, p.len, p.c), chunk_begin(ch + 1, p.len, p.c),
-                                   p.probe, lane, start_state, start_live, dead, p.maps + ch * p.stride,
-                                   p.dinfo + ch, p.status, out_pos, out_state, alive);
-}
-
-// The same for two independent chains, interleaved so their lookups overlap.
-template <class LUT>
-__device__ __forceinline__ void run_granule2(const LUT &T, uint32_t &s0, uint32_t a0, uint32_t &s1,
-                                             uint32_t a1) {
-    const uint4 x = lds_v4(a0), y = lds_v4(a1);
-    const uint32_t w0[4] = {x.x, x.y, x.z, x.w}, w1[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        uint32_t c0[8], c1[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int b = h * 8 + q;
-            c0[q] = T.cls_at(w0[b >> 2], b & 3);
-            c1[q] = T.cls_at(w1[b >> 2], b & 3);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            s0 = T.next(s0, c0[q]);
-            s1 = T.next(s1, c1[q]);
-        }
-    }
-}
-
-// Cooperative text path with two chunks per lane.  A warp owns 64 consecutive chunks: lane l
-// finishes chunks l and 32 + l after the speculative phase, interleaving the two runs.  Each
-// round the warp loads one 32-byte window of each of its 64 chunks with coalesced 16-byte loads
-// (16 chunks' windows per instruction, two lanes per window), one round ahead, into a shared
-// buffer whose windows sit 48 bytes apart (3 granules, odd: conflict-free 16-byte reads).
-constexpr uint32_t kC2Win = 32;
-constexpr uint32_t kC2Stride = 48;
-constexpr uint32_t kWarpCoop2Bytes = 64 * kC2Stride;
-
-template <int R, class LUT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1) rid_reach2_kernel(ReachArgs p, int table_in_smem,
-                                                             uint32_t staging_offset) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    const Automaton &A = p.A;
-    LUT T;
-    T.setup(A, smem, table_in_smem != 0);
-    __syncthreads();
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t stg = smem_addr(smem) + staging_offset + (threadIdx.x >> 5) * kWarpCoop2Bytes;
-    const uint32_t dead = T.enc(A.n);
-    const uint64_t n_tasks = (static_cast<uint64_t>(p.c) + 63) / 64;
-    const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-    const uint64_t lim = p.len & ~static_cast<uint64_t>(15);
-
-    uint32_t start_state[R];
-    uint32_t start_live = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t a = r * 32 + lane;
-        start_state[r] = a < A.k ? T.enc(A.slot_state[a]) : dead;
-        if (r * 32 < static_cast<int>(A.k)) start_live |= 1u << r;
-    }
-
-    for (uint64_t task = warp0; task < n_tasks; task += n_warps) {
-        const uint64_t chunk0 = task * 64;
-        uint64_t pos[2] = {0, 0}, end[2] = {0, 0};
-        uint32_t s[2] = {dead, dead};
-        uint32_t alive[2][R];
-        bool pend[2] = {false, false};
-#pragma unroll
-        for (int nb = 0; nb < 2; ++nb) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) alive[nb][r] = 0;
-            for (uint32_t j = 0; j < 32; ++j) {
-                const uint64_t ch = chunk0 + nb * 32 + j;
-                if (ch >= p.c) break;
-                uint64_t cp;
-                uint32_t cs;
-                uint32_t al[R];
-                if (speculate_chunk<R, LUT>(p, T, ch, lane, start_state, start_live, dead, &cp, &cs, al)) {
-                    if (lane == j) {
-                        pos[nb] = cp;
-                        s[nb] = cs;
-                        pend[nb] = true;
-#pragma unroll
-                        for (int r = 0; r < R; ++r) alive[nb][r] = al[r];
-                    }
-                }
-            }
-        }
-        // ---------------- converged phase: two chains per lane over shared windows
-        uint64_t wb[2];
-        uint32_t nwin[2];
-#pragma unroll
-        for (int nb = 0; nb < 2; ++nb) {
-            if (pend[nb]) end[nb] = chunk_begin(chunk0 + nb * 32 + lane + 1, p.len, p.c);
-            const uint64_t stop = min(end[nb], lim);
-            wb[nb] = pos[nb] & ~static_cast<uint64_t>(15);
-            nwin[nb] = (pend[nb] && wb[nb] < stop)
-                           ? static_cast<uint32_t>((stop - wb[nb] + kC2Win - 1) / kC2Win) : 0;
-        }
-        const uint32_t max_win = __reduce_max_sync(kFull, max(nwin[0], nwin[1]));
-        if (max_win) {
-            const uint32_t g = lane & 1;
-            uint4 v[4];
-            // instruction u loads window j = 16u + (lane >> 1) (chunk chunk0 + j), granule g
-            auto fetch = [&](uint32_t r) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int src = (16 * u + (lane >> 1)) & 31;
-                    const int nb = u >> 1;
-                    const uint64_t a = __shfl_sync(kFull, wb[nb], src) + static_cast<uint64_t>(kC2Win) * r + 16 * g;
-                    const uint32_t nw = __shfl_sync(kFull, nwin[nb], src);
-                    v[u] = (r < nw && a + 16 <= lim) ? __ldg(reinterpret_cast<const uint4 *>(p.text + a))
-                                                     : make_uint4(0, 0, 0, 0);
-                }
-            };
-            auto stash = [&]() {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t j = 16 * u + (lane >> 1);
-                    const uint32_t addr = stg + j * kC2Stride + 16 * g;
-                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
-                                 ::"r"(addr), "r"(v[u].x), "r"(v[u].y), "r"(v[u].z), "r"(v[u].w) : "memory");
-                }
-            };
-            fetch(0);
-            stash();
-            __syncwarp();
-            const uint32_t sb0 = stg + lane * kC2Stride, sb1 = stg + (32 + lane) * kC2Stride;
-            for (uint32_t r = 0; r < max_win; ++r) {
-                if (r + 1 < max_win) fetch(r + 1);
-                bool full[2], have[2];
-                uint64_t lo[2], hi[2], ws[2];
-#pragma unroll
-                for (int nb = 0; nb < 2; ++nb) {
-                    ws[nb] = wb[nb] + static_cast<uint64_t>(kC2Win) * r;
-                    have[nb] = r < nwin[nb] && s[nb] != dead;
-                    const uint64_t stop = min(end[nb], lim);
-                    lo[nb] = max(pos[nb], ws[nb]);
-                    hi[nb] = min(stop, ws[nb] + kC2Win);
-                    full[nb] = have[nb] && lo[nb] == ws[nb] && hi[nb] == ws[nb] + kC2Win;
-                }
-                if (full[0] && full[1]) {
-                    run_granule2(T, s[0], sb0, s[1], sb1);
-                    run_granule2(T, s[0], sb0 + 16, s[1], sb1 + 16);
-                } else {
-#pragma unroll
-                    for (int nb = 0; nb < 2; ++nb) {
-                        if (!have[nb]) continue;
-                        const uint32_t sb = nb ? sb1 : sb0;
-                        if (full[nb]) {
-                            s[nb] = run_granule(T, s[nb], sb);
-                            s[nb] = run_granule(T, s[nb], sb + 16);
-                        } else {
-                            for (uint64_t q = lo[nb]; q < hi[nb]; ++q)
-                                s[nb] = T.next(s[nb], T.cls_of(lds_u8(sb + static_cast<uint32_t>(q - ws[nb]))));
-                        }
-                    }
-                }
-#pragma unroll
-                for (int nb = 0; nb < 2; ++nb)
-                    if (have[nb]) pos[nb] = hi[nb];
-                __syncwarp();
-                if (r + 1 < max_win) {
-                    stash();
-                    __syncwarp();
-                }
-            }
-        }
-        // tails past the last 16-byte boundary of the text, then rows and summaries
-#pragma unroll
-        for (int nb = 0; nb < 2; ++nb) {
-            if (!pend[nb]) continue;
-            while (pos[nb] < end[nb] && s[nb] != dead) {
-                s[nb] = T.next(s[nb], T.cls_of(__ldg(p.text + pos[nb])));
-                ++pos[nb];
-            }
-            const uint64_t ch = chunk0 + nb * 32 + lane;
-            bool any = false;
-#pragma unroll
-            for (int r = 0; r < R; ++r) any |= alive[nb][r] != 0;
-            const uint32_t sid = T.id(s[nb]);
-            const uint16_t val = s[nb] == dead ? kUndef : static_cast<uint16_t>(sid);
-            write_row<R>(p.maps + ch * p.stride, A.k, alive[nb], val);
-            p.dinfo[ch] = (any && s[nb] != dead) ? ((1u << 16) | sid) : static_cast<uint32_t>(kUndef);
-        }
-    }
-}
 
 // ------------------------------------------------------------------------------- join
 struct JoinArgs {
@@ -1160,80 +794,12 @@ DeviceScratch *scratch_for(const ridfa_program *P, int dev, size_t bytes, int *e
     return S;
 }
 
-enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3, kModePart16 = 4, kModeFlat = 5,
-                       kModeRep16x4 = 6, kModeRep16x4C = 7 };
-
-// How one reach launch is laid out: table layout, text path, block/grid, shared memory.
-struct ReachPlan {
-    uint32_t mode = kModePlain;
-    int R = 1;
-    int tis = 0;                 // compact table in shared memory (Plain only)
-    int path = kPathGlobal;      // how the converged phase reads the text
-    int block = 256;
-    int grid = 1;
-    size_t smem = 0;
-    uint32_t staging_offset = 0;
-    bool pslot = false;          // per-chunk start states (ReachArgs::piece_slots; R = 1 only)
-};
-
-template <int R, int PATH = kPathCoop>
-constexpr int block_cap() { return R <= 4 && PATH != kPathCoopSet ? 1024 : 512; }
-
-// Launch (or, with per_sm != nullptr, size) one instantiation of the reach kernel.
-template <int R>
-constexpr int block_cap2() { return R <= 4 ? 768 : 512; }
-
-template <int R, class LUT, int PATH>
-cudaError_t reach_one(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
-    using KernT = void (*)(ReachArgs, int, uint32_t);
-    KernT kern;
-    if constexpr (PATH == kPathCoop2) kern = rid_reach2_kernel<R, LUT, block_cap2<R>()>;
-    else kern = rid_reach_kernel<R, LUT, block_cap<R, PATH>(), PATH>;
-    if (pl.pslot) {
-        if constexpr (R == 1 && (PATH == kPathGlobal || PATH == kPathCoop || PATH == kPathCoopSet))
-            kern = rid_reach_kernel<1, LUT, block_cap<1, PATH>(), PATH, true>;
-        else
-            return cudaErrorInvalidValue;
-    }
-    cudaError_t e = ensure_smem_cap(reinterpret_cast<const void *>(kern), pl.smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, pl.block, pl.smem);
-    kern<<<pl.grid, pl.block, pl.smem, st>>>(a, pl.tis, pl.staging_offset);
-    return cudaGetLastError();
-}
-
-template <class LUT, int PATH>
-cudaError_t reach_r(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
-    switch (pl.R) {
-        case 1: return reach_one<1, LUT, PATH>(a, pl, st, per_sm);
-        case 2: return reach_one<2, LUT, PATH>(a, pl, st, per_sm);
-        case 4: return reach_one<4, LUT, PATH>(a, pl, st, per_sm);
-        default: return reach_one<8, LUT, PATH>(a, pl, st, per_sm);
-    }
-}
-
-template <int PATH>
-cudaError_t reach_m(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
-    switch (pl.mode) {
-        case kModeRep16: return reach_r<LutRep<true>, PATH>(a, pl, st, per_sm);
-        case kModeRep32: return reach_r<LutRep<false>, PATH>(a, pl, st, per_sm);
-        case kModePart16: return reach_r<LutPart, PATH>(a, pl, st, per_sm);
-        case kModeRep16x4: return reach_r<LutRep16x4, PATH>(a, pl, st, per_sm);
-        case kModeRep16x4C:
-            // (the compact class table serves the set path and plain global loads only)
-            if constexpr (PATH == kPathCoopSet || PATH == kPathGlobal) return reach_r<LutRep16x4C, PATH>(a, pl, st, per_sm);
-            else return cudaErrorInvalidValue;
-        case kModePlain: return reach_r<LutPlain, PATH>(a, pl, st, per_sm);
-        default: return reach_r<LutFlat, PATH>(a, pl, st, per_sm);
-    }
-}
-
 cudaError_t reach_dispatch(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
     switch (pl.path) {
-        case kPathCoop: return reach_m<kPathCoop>(a, pl, st, per_sm);
-        case kPathCoop2: return reach_m<kPathCoop2>(a, pl, st, per_sm);
-        case kPathCoopSet: return reach_m<kPathCoopSet>(a, pl, st, per_sm);
-        default: return reach_m<kPathGlobal>(a, pl, st, per_sm);
+        case kPathCoop: return reach_path_coop(a, pl, st, per_sm);
+        case kPathCoop2: return reach_path_coop2(a, pl, st, per_sm);
+        case kPathCoopSet: return reach_path_set(a, pl, st, per_sm);
+        default: return reach_path_global(a, pl, st, per_sm);
     }
 }
 
@@ -1248,6 +814,7 @@ cudaError_t piece_dispatch(const ReachArgs &a, const ReachPlan &pl, int sms, cud
         case kModePart16: return piece_r<LutPart>(pl.R, a, grid, smem, pl.tis, st);
         case kModeRep16x4: return piece_r<LutRep16x4>(pl.R, a, grid, smem, pl.tis, st);
         case kModeRep16x4C: return piece_r<LutRep16x4C>(pl.R, a, grid, smem, pl.tis, st);
+        case kModePair: return piece_r<LutPair>(pl.R, a, grid, smem, pl.tis, st);
         case kModePlain: return piece_r<LutPlain>(pl.R, a, grid, smem, pl.tis, st);
         default: return piece_r<LutFlat>(pl.R, a, grid, smem, pl.tis, st);
     }
@@ -1282,7 +849,7 @@ cudaError_t lookback_dispatch(const LookbackArgs &a, int sms, cudaStream_t st) {
 // shared memory when the text is 16-byte aligned and the staging buffers fit next to the table;
 // one block per SM with as many warps as fit; a grid of one wave.
 int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *text,
-               const ReachArgs &ra, int sms, ReachPlan *out) {
+               const ReachArgs &ra, int sms, ReachPlan *out, bool allow_pair = true) {
     ReachPlan pl;
     pl.R = A.k <= 32 ? 1 : A.k <= 64 ? 2 : A.k <= 128 ? 4 : 8;
     const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024;
@@ -1293,11 +860,12 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // slower -- its gathers conflict less, but its larger footprint leaves fewer warps and the
     // time goes to run imbalance, not conflicts)
     const size_t plain = LutPlain::smem_bytes(A), flat = LutFlat::smem_bytes(A), rep16x4 = LutRep16x4::smem_bytes(A),
-                 rep16x4c = LutRep16x4C::smem_bytes(A);
+                 rep16x4c = LutRep16x4C::smem_bytes(A), pair = LutPair::smem_bytes(A);
     const bool ok16 = LutRep<true>::fits16(A) && rep16 <= limit, ok32 = rep32 <= limit,
                okp = LutPart::fits(A) && part16 <= limit, okplain = LutPlain::fits(A) && plain <= limit,
                ok16x4 = LutRep16x4::fits(A) && rep16x4 <= limit,
-               ok16x4c = LutRep16x4C::fits(A) && rep16x4c + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit;
+               ok16x4c = LutRep16x4C::fits(A) && rep16x4c + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit,
+               okpair = LutPair::fits(A) && pair + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit;
     // replicated layouts that leave room for at least 16 warps' staging come first; a 32-bit table
     // that leaves fewer is taken only when no scaled 16-bit one fits (measured: a 6-warp 32-bit
     // table ran at a third of the speed of a 26-warp scaled one)
@@ -1319,18 +887,27 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
             const size_t w_part = warps_beside(part16);
             if (4 * w_part >= 5 * w_cf) mode = kModePart16;
         }
+        // small automata take two bytes per transition lookup when the pair table leaves room for
+        // a full block's staging (regexp family k = 3..5: 2,716 -> 3,088 GB/s; the C1 RE on 1 GiB:
+        // 2,507 -> 2,911); not for the lockstep pieces, whose kernel steps one byte at a time
+        // (C1 on 1 MiB: 20.6 -> 17.6 GB/s with pairs)
+        const uint32_t tp = tuning ? tuning->text_path : 0;
+        if (allow_pair && okpair && (tp == 0 || tp == 1 || tp == 3) &&
+            pair + 32 * static_cast<size_t>(kWarpCoopBytes) <= limit)
+            mode = kModePair;
     }
     if (mode == kModeRep16x4 && !ok16x4) return RIDFA_E_ARG;
     if (mode == kModeRep16x4C && !ok16x4c) return RIDFA_E_ARG;
+    if (mode == kModePair && !okpair) return RIDFA_E_ARG;
     if (mode == kModePlain && !okplain) mode = kModeFlat;    // the compact table, through generic loads
     if ((mode == kModeRep16 && !ok16) || (mode == kModeRep32 && !ok32) || (mode == kModePart16 && !okp))
         return RIDFA_E_ARG;
-    if (mode < kModePlain || mode > kModeRep16x4C) return RIDFA_E_ARG;
+    if (mode < kModePlain || mode > kModePair) return RIDFA_E_ARG;
     pl.mode = mode;
     pl.tis = (mode == kModeFlat && flat <= limit) ? 1 : 0;
     const size_t table_smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : mode == kModePart16 ? part16
                               : mode == kModeRep16x4 ? rep16x4 : mode == kModeRep16x4C ? rep16x4c
-                              : mode == kModePlain ? plain : (pl.tis ? flat : 256);
+                              : mode == kModePair ? pair : mode == kModePlain ? plain : (pl.tis ? flat : 256);
     const int cap = pl.R <= 4 ? 1024 : 512;
     const uint32_t text_path = tuning ? tuning->text_path : 0;
     if (text_path > 5) return RIDFA_E_ARG;
@@ -1368,8 +945,10 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     if (pl.path == kPathCoop && !(aligned && w_coop)) return RIDFA_E_ARG;
     if (pl.path == kPathCoop2 && !(aligned && w_coop2)) return RIDFA_E_ARG;
     if (pl.path == kPathCoopSet && !(aligned && w_set)) return RIDFA_E_ARG;
-    // the compact class table is built for the set path (and plain global loads)
+    // the compact class table is built for the set path (and plain global loads), two-byte steps
+    // for the single-run cooperative path (and plain global loads)
     if (mode == kModeRep16x4C && pl.path != kPathCoopSet && pl.path != kPathGlobal) return RIDFA_E_ARG;
+    if (mode == kModePair && pl.path != kPathCoop && pl.path != kPathGlobal) return RIDFA_E_ARG;
     const int warps_fit = pl.path == kPathCoop      ? w_coop
                           : pl.path == kPathCoopSet ? w_set
                           : pl.path == kPathCoop2 ? w_coop2
@@ -1508,7 +1087,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
         ras[g] = ReachArgs{Ag, d_text, len, static_cast<uint32_t>(pieces), nullptr, nullptr, nullptr, 8,
                            nullptr, nullptr, lookback ? 32u : spc > 1 ? NS : H.k, nullptr};
         if (tuning && tuning->probe_interval) ras[g].probe = tuning->probe_interval;
-        err = plan_reach(ras[g].A, tuning, d_text, ras[g], sms, &plans[g]);
+        err = plan_reach(ras[g].A, tuning, d_text, ras[g], sms, &plans[g], !lockstep);
         if (err != RIDFA_OK) return err;
         plans[g].pslot = lookback;
         // warps past the last 32-chunk task never write their run list (the lockstep kernel has none)

@@ -10,16 +10,9 @@
 #include "ridfa_internal.h"
 
 namespace ridfa {
-namespace {
 
-constexpr uint32_t kFull = 0xFFFFFFFFu;
-constexpr uint16_t kUndef = 0xFFFF;
-constexpr uint32_t kStatusWide = 1u;      // some chunk has > 32 distinct end states
-constexpr uint32_t kStatusBad = 2u;       // a device consistency check failed
-constexpr int kMaxD = 32;                 // distinct end states handled by the matrix join
-constexpr int kJoinThreads = 256;
-static_assert(kPartialWords == 1 + kMaxD, "join partial layout");
-
+// (the plain structs below have one definition for every translation unit: the reach launches
+// of each text path are compiled in a unit of their own)
 struct Automaton {            // device view of one automaton
     const uint16_t *trans;    // [(n+1) * C]
     const uint8_t *classmap;  // [256]
@@ -29,12 +22,6 @@ struct Automaton {            // device view of one automaton
     uint32_t n, C, k, kw, q0_slot;
 };
 
-__host__ __device__ inline uint64_t chunk_begin(uint64_t i, uint64_t len, uint64_t c) {
-    // floor(i * len / c) without 128-bit products: i*(len/c) + (i*(len%c))/c
-    return i * (len / c) + (i * (len % c)) / c;
-}
-
-// ------------------------------------------------------------------------------ reach
 // A run handed from the speculative phase to one lane: chunk j of the warp's task, resume
 // position, state (policy encoding), and the group of slots that share it.
 struct RunEntry {
@@ -43,13 +30,6 @@ struct RunEntry {
     uint16_t chunk;
     uint16_t group;
 };
-constexpr int kMaxRun = 8;              // distinct live states one chunk may hand off
-constexpr uint32_t kMultiMin = 64;      // speculated bytes before a multi-run hand-off is tried
-constexpr uint32_t kRunsPerWarp = 32 * kMaxRun;
-// per-warp words of the finals area: the final state of each run, then the alive bits of the
-// task's hand-offs (word 32*r + lane: bit j = slot 32*r + lane alive at chunk j's hand-off)
-constexpr uint32_t kFinalsPerWarp = kRunsPerWarp + 32 * 8;
-static_assert(kMaxRun <= 8, "group tags keep the group in the low 3 bits");
 
 struct ReachArgs {
     Automaton A;
@@ -60,13 +40,44 @@ struct ReachArgs {
     uint32_t *dinfo;          // [c]: (m << 16) | min defined end state (0xFFFF if none)
     uint32_t *status;
     uint32_t probe;
-    RunEntry *runs;           // [grid warps][kRunsPerWarp], or null: only single-run hand-offs
+    RunEntry *runs;           // [grid warps][32 * 8], or null: only single-run hand-offs
     uint32_t *finals;         // [grid warps][kFinalsPerWarp]
     uint32_t stride;          // entries between consecutive rows of maps (A.k, or wider when the
                               // slots are one group of a larger row)
     const uint16_t *piece_slots;   // [c][32] per-chunk start states (0xFFFF: none), or null: the
                                    // slots' start states A.slot_state for every chunk
 };
+
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint16_t kUndef = 0xFFFF;
+constexpr uint32_t kStatusWide = 1u;      // some chunk has > 32 distinct end states
+constexpr uint32_t kStatusBad = 2u;       // a device consistency check failed
+constexpr int kMaxD = 32;                 // distinct end states handled by the matrix join
+constexpr int kJoinThreads = 256;
+static_assert(kPartialWords == 1 + kMaxD, "join partial layout");
+
+
+__host__ __device__ inline uint64_t chunk_begin(uint64_t i, uint64_t len, uint64_t c) {
+    // floor(i * len / c) without 128-bit products: i*(len/c) + (i*(len%c))/c
+    return i * (len / c) + (i * (len % c)) / c;
+}
+
+// ------------------------------------------------------------------------------ reach
+constexpr int kMaxRun = 8;              // distinct live states one chunk may hand off
+// speculated bytes before a multi-run hand-off is tried: on the set path a lane carries all of a
+// chunk's runs in one pass, so handing off early is cheap there (the codon RE: 16 bytes 7.7 %
+// faster than 64); where each run takes a lane of its own, a late hand-off lets more runs merge
+// first (the any-field record lines lost a third at 16)
+constexpr uint32_t kMultiMin = 64;
+constexpr uint32_t kMultiMinSet = 16;
+constexpr uint32_t kRunsPerWarp = 32 * kMaxRun;
+// per-warp words of the finals area: the final state of each run, then the alive bits of the
+// task's hand-offs (word 32*r + lane: bit j = slot 32*r + lane alive at chunk j's hand-off)
+constexpr uint32_t kFinalsPerWarp = kRunsPerWarp + 32 * 8;
+static_assert(kMaxRun <= 8, "group tags keep the group in the low 3 bits");
+
 
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
     uint32_t v;
@@ -317,6 +328,67 @@ struct LutRep16x4T {
 using LutRep16x4 = LutRep16x4T<false>;
 using LutRep16x4C = LutRep16x4T<true>;
 
+// Two-byte transitions (the super-transition tables among the compatible optimisations of the
+// paper's conclusion, Sec. 5): the converged runs take the text two bytes per lookup.  Beside the
+// lane-replicated class table (word b*32 + l = class(b) * 128) sits one lane-replicated table of
+// 16-bit entries with a column for every pair of classes (c1, c2), entry delta(delta(s, c1), c2),
+// and one for every single class c, entry delta(s, c): NP = C*C + C columns.  States are paired so
+// that a pair column's offset is the sum of the two class words:
+//   entry (s, p) at byte ((s >> 1) * NP + p) * 128 + l * 4 + (s & 1) * 2,
+//   enc(s) = (s >> 1) * NP * 128 + (s & 1) * 2,
+// so a pair step is s' = T[s + cw1 * C + cw2] (one IMAD, one add, one ld.shared.u16) and a single
+// step s' = T[s + C*C*128 + cw] (one add, one load).  A 16-byte granule then costs 16 class lookups
+// and 8 transition lookups instead of 16 + 16.  Fits small automata only: (P/2 + 1) * NP <= 511.
+struct LutPair {
+    static constexpr bool kPairs = true;
+    uint32_t lc, lt, lt1;     // this lane's class copy; its transition copy (pairs, singles)
+    uint32_t C, NP;
+    static uint32_t np_of(const Automaton &A) { return A.C * A.C + A.C; }
+    static size_t smem_bytes(const Automaton &A) {
+        return 256 * 128 + static_cast<size_t>((A.n + 2) / 2) * np_of(A) * 128;
+    }
+    static bool fits(const Automaton &A) {
+        return (static_cast<uint64_t>(A.n / 2) + 1) * np_of(A) * 128 <= 0xFFFF;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return (id >> 1) * NP * 128 + (id & 1) * 2; }
+    __device__ __forceinline__ uint32_t id(uint32_t e) const { return ((e >> 7) / NP) * 2 + ((e >> 1) & 1); }
+    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+        C = A.C;
+        NP = C * C + C;
+        const uint32_t base_c = smem_addr(smem);
+        const uint32_t base_t = base_c + 256 * 128;
+        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) sts_u32(base_c + i * 4, A.classmap[i >> 5] * 128u);
+        const uint32_t n = A.n;               // the dead state: row n maps to itself
+        auto step = [&](uint32_t st, uint32_t c) { return st >= n ? n : static_cast<uint32_t>(A.trans[st * C + c]); };
+        auto value = [&](uint32_t st, uint32_t col) {
+            if (st > n) st = n;
+            const uint32_t t = col < C * C ? step(step(st, col / C), col % C) : step(st, col - C * C);
+            return enc(t);
+        };
+        const uint32_t words = ((n + 2) / 2) * NP;
+        for (uint32_t i = threadIdx.x; i < words * 32; i += blockDim.x) {
+            const uint32_t w = i >> 5;
+            const uint32_t sp = w / NP, col = w % NP;
+            sts_u32(base_t + i * 4, value(2 * sp, col) | (value(2 * sp + 1, col) << 16));
+        }
+        const uint32_t lane = threadIdx.x & 31;
+        lc = base_c + lane * 4;
+        lt = base_t + lane * 4;
+        lt1 = lt + C * C * 128;
+    }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return lds_u16(lt1 + s + c); }
+    __device__ __forceinline__ uint32_t next2(uint32_t s, uint32_t c1, uint32_t c2) const {
+        return lds_u16(lt + s + (c1 * C + c2));
+    }
+};
+
+template <class LUT, class = void>
+struct has_pairs { static constexpr bool value = false; };
+template <class LUT>
+struct has_pairs<LUT, decltype(void(LUT::kPairs))> { static constexpr bool value = LUT::kPairs; };
+
 // Half-replicated tables, for transition tables too large to replicate 32 times: the class table
 // as in LutRep (32 copies, conflict-free), the transition table in F = 16 copies, lane l reading
 // copy l & 15.  Entry (s, c) sits at byte ((s * Cp/2 + c/2) * 16 + (l & 15)) * 4 + (c & 1) * 2, so
@@ -393,7 +465,7 @@ __device__ __forceinline__ void write_row(uint16_t *row, uint32_t k, const uint3
 // Speculative phase of one chunk text[beg, end) by the whole warp (lanes = runs; slot
 // a = 32*r + lane in register r).  Every `probe` bytes the warp drops registers whose runs are all
 // dead and checks whether the live runs sit in one state (redux.sync min == max).  With `multi`
-// set, once kMultiMin bytes have been speculated it also hands off as soon as the live runs sit in
+// set, once MULTI_MIN bytes have been speculated it also hands off as soon as the live runs sit in
 // at most kMaxRun distinct states, each as a run of its own.
 //
 // Return m >= 1 (handed off before `end`): *out_pos is the resume position, lane g < m holds the
@@ -403,7 +475,7 @@ __device__ __forceinline__ void write_row(uint16_t *row, uint32_t k, const uint3
 // dead one, to be replaced once the runs end.
 // Return 0: the chunk finished here; its map row (`row`, k entries) and its D_i summary
 // (`*dinfo_slot`) are written.
-template <int R, class LUT>
+template <int R, class LUT, uint32_t MULTI_MIN = kMultiMin>
 __device__ __forceinline__ int speculate(const LUT &T, const Automaton &A, const uint8_t *text,
                                          uint64_t beg, uint64_t end, uint32_t probe, uint32_t lane,
                                          const uint32_t (&start_state)[R], uint32_t start_live,
@@ -445,7 +517,7 @@ __device__ __forceinline__ int speculate(const LUT &T, const Automaton &A, const
             }
             break;
         }
-        if (multi && pos < end && pos - beg >= kMultiMin) {
+        if (multi && pos < end && pos - beg >= MULTI_MIN) {
             // the distinct live states in ascending order, lane g taking the g-th, while there
             // are at most kMaxRun of them
             uint32_t cnt = 0, cur = 0, mine = dead;
@@ -583,8 +655,13 @@ __device__ __forceinline__ uint32_t run_granule(const LUT &T, uint32_t s, uint32
     uint32_t cl[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) cl[q] = T.cls_at(w[q >> 2], q & 3);
+    if constexpr (has_pairs<LUT>::value) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
+        for (int q = 0; q < 16; q += 2) s = T.next2(s, cl[q], cl[q + 1]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) s = T.next(s, cl[q]);
+    }
     return s;
 }
 
@@ -695,7 +772,9 @@ template <class LUT, int M>
 __device__ __forceinline__ void set_window(const LUT &T, uint32_t sb, uint32_t sw, uint32_t o0, uint32_t o1,
                                            uint32_t (&s)[kMaxRun]) {
     if (o0 == 0 && o1 == kCoopWin) {
-#pragma unroll
+        // (one granule of code per M, not four: the eight specialisations share the instruction
+        // cache, and the unrolled form measured slower for it)
+#pragma unroll 1
         for (uint32_t q16 = 0; q16 < kCoopWin / 16; ++q16) {
             const uint4 x = lds_v4(sb + 16 * (q16 ^ sw));
             const uint32_t w[4] = {x.x, x.y, x.z, x.w};

@@ -1,0 +1,9 @@
+// Reach-kernel instantiations of one text path (kPathCoop2): every table layout and interface
+// register count it supports.
+#include "ridfa_reach.cuh"
+
+namespace ridfa {
+cudaError_t reach_path_coop2(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, int *per_sm) {
+    return reach_m<kPathCoop2>(a, pl, st, per_sm);
+}
+}  // namespace ridfa

@@ -491,3 +491,42 @@ def test_compact_class_table_layout():
         with pytest.raises(lib.RidfaError) as e:
             lib.ridfa_recognize(prog, to_device(x), x.size, 1000, tuning=dict(table_mode=7, text_path=tp))
         assert e.value.code == -1
+
+
+def test_two_byte_step_layout():
+    """Table layout 8 (two-byte steps: one transition lookup per pair of bytes in the converged
+    phase, single steps at ragged edges): every row equals the oracle's on the C1 RE and the
+    regexp family k = 3, 4, 5, aligned (staged, whole granules of pairs) and unaligned (global
+    loads) texts, bytes outside the alphabet, few chunks (pieces); automata too large for the
+    layout, and the set path, refuse it."""
+    for re_src, x in ((textgen.C1_RE, textgen.c1_text(300_001, seed=301)),
+                      (textgen.regexp_family_re(3), textgen.regexp_family_text(300_001, seed=302)),
+                      (textgen.regexp_family_re(4), textgen.regexp_family_text(200_003, seed=303)),
+                      (textgen.regexp_family_re(5), textgen.regexp_family_text(200_005, seed=304))):
+        for c in (1, 7, 1000, 4099):
+            check(re_src, x, c, rows=list(range(c)) if c <= 1000 else None, tuning=dict(table_mode=8))
+        y, _ = textgen.mutate(x, seed=305, n_subs=3, alphabet=b"ACGTabN\n")
+        check(re_src, y, 1000, rows=list(range(1000)), tuning=dict(table_mode=8))
+        check(re_src, x, 1000, rows=list(range(1000)), tuning=dict(table_mode=8, text_path=1))
+        prog = lib.ridfa_compile(re_src)
+        o, ser = oracle(re_src)
+        base = torch.from_numpy(np.concatenate([np.zeros(16, np.uint8), x])).to("cuda:0")
+        z = x[5:]
+        maps = torch.empty((300, prog.info["k"]), dtype=torch.int16, device="cuda:0")
+        acc = lib.ridfa_recognize(prog, base[16 + 5:], z.size, 300, tuning=dict(table_mode=8), d_chunk_maps=maps)
+        assert acc == ser.accepts(z)
+        got = maps.cpu().numpy().view(np.uint16)
+        want = o.lambda_rows(z, 300, [0, 1, 150, 298, 299])
+        for i in want:
+            assert np.array_equal(got[i], want[i])
+    prog = lib.ridfa_compile(textgen.C3_RE)
+    x3 = textgen.c3_text(1 << 16, seed=306)
+    for tu in (dict(table_mode=8), dict(table_mode=8, text_path=5)):
+        with pytest.raises(lib.RidfaError) as e:
+            lib.ridfa_recognize(prog, to_device(x3), x3.size, 100, tuning=tu)
+        assert e.value.code == -1
+    prog = lib.ridfa_compile(textgen.C1_RE)
+    x1 = textgen.c1_text(1 << 16, seed=307)
+    with pytest.raises(lib.RidfaError) as e:
+        lib.ridfa_recognize(prog, to_device(x1), x1.size, 100, tuning=dict(table_mode=8, text_path=5))
+    assert e.value.code == -1
