@@ -578,6 +578,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dfa", action="store_true")
     ap.add_argument("--no-counts", action="store_true", help="skip the host transition counters")
+    ap.add_argument("--nfa", action="store_true",
+                    help="also time the NFA variant of the classic algorithm (Sec. 2) on the same text "
+                         "and count its transitions (Table 3's NFA columns)")
     ap.add_argument("--ablation", action="store_true",
                     help="also time the unminimised interface (every NFA state a slot)")
     ap.add_argument("--table-mode", type=int, default=0,
@@ -731,6 +734,18 @@ def main():
                                 "frac": round(text_rate / lut_rate, 4),
                                 "note": "ridfa_bench_smem_gather: 2 lane-private gathers per byte, all SMs"}}
 
+    # the NFA variant (Sec. 2): every position-NFA state a start state, sets simulated per start
+    nfa = None
+    if args.nfa and info["n_nfa"] <= 128:
+        assert lib.ridfa_recognize_nfa(prog, d_text, n, c, stream=stream) == acc, "RID and NFA variant disagree"
+        k_nfa = 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_nfa):
+            lib.ridfa_recognize_nfa(prog, d_text, n, c, stream=stream)
+        nfa = {"value": round(n * k_nfa / (time.perf_counter() - t0) / 1e9, 3), "unit": "GB/s",
+               "note": "ridfa_recognize_nfa, synchronous calls (reach + composition join + accept read back)"}
+
     # the effect of interface minimisation (Sec. 3.4): the same text with I^B = every singleton
     ablation = None
     if args.ablation:
@@ -777,6 +792,10 @@ def main():
             work.update({"dfa_w_conv_per_byte": round(dc["w_conv"] / n, 5),
                          "dfa_w_paper_per_byte": round(dc["w_paper"] / n, 5),
                          "transition_ratio_dfa_over_rid": round(dc["w_paper"] / max(rc["w_paper"], 1), 4)})
+        if args.nfa and info["n_nfa"] <= 128:
+            nc = lib.ridfa_count_transitions(prog, hx, c, nfa=True)
+            work.update({"nfa_w_paper_per_byte": round(nc["w_paper"] / n, 5),
+                         "transition_ratio_nfa_over_rid": round(nc["w_paper"] / max(rc["w_paper"], 1), 4)})
         work["count_s"] = round(time.perf_counter() - t0, 2)
         lpb = 1 + rc["w_conv"] / n
         roofline["smem_gather"]["lookups_per_byte"] = round(lpb, 5)
@@ -824,7 +843,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "dfa_value": round(dfa_value, 3) if dfa_value else None,
                 "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "work": work,
-                "interface_ablation": ablation,
+                "interface_ablation": ablation, "nfa_variant": nfa,
                 "batched": batched, "served": served,
                 "gpu_launches": 2 * args.steps}
         print(json.dumps(line), flush=True)

@@ -201,7 +201,10 @@ int ridfa_join_scan(const ridfa_program *prog, const uint16_t *d_maps, uint32_t 
 /* Transition counts of the reach phase, computed on the host (diagnostics).
  * Chunk 1 runs from {q0}'s slot only, every other chunk from every interface slot (Sec. 3.2);
  * which = 1 counts the all-states DFA comparator instead (chunk 1 from q0, the others from
- * every state of the minimal DFA, Sec. 2). */
+ * every state of the minimal DFA, Sec. 2); which = 2 the NFA variant (chunk 1 from q0, the others
+ * from every position-NFA state, each start's set of active states followed on its own: a step
+ * from the set S on a byte of class c executes sum over q in S of |Follow(q) n positions(c)|
+ * transitions, counted in w_paper; w_conv then counts the active NFA states processed). */
 typedef struct {
     uint64_t w_paper;   /* transitions with every run followed on its own, undefined moves not
                            counted: the paper's measure (Sec. 1, Fig. 1) */
@@ -212,7 +215,8 @@ typedef struct {
 } ridfa_transition_counts;
 
 /* h_text: host pointer to len bytes; 1 <= n_chunks <= len; n_threads host threads over the
- * chunks (0 = all hardware threads).  Errors: E_ARG, E_NO_DFA, E_CHUNKS, E_NOMEM. */
+ * chunks (0 = all hardware threads).  Errors: E_ARG, E_NO_DFA, E_UNSUPPORTED (which = 2 with more
+ * than 128 NFA states), E_CHUNKS, E_NOMEM. */
 int ridfa_count_transitions(const ridfa_program *prog, int which, const uint8_t *h_text, size_t len,
                             uint32_t n_chunks, uint32_t n_threads, ridfa_transition_counts *out);
 
@@ -264,6 +268,23 @@ int ridfa_recognize_dfa(const ridfa_program *prog, const uint8_t *d_text, size_t
 int ridfa_recognize_dfa_async(const ridfa_program *prog, const uint8_t *d_text, size_t len,
                               uint32_t n_chunks, const ridfa_tuning *tuning, uint8_t *d_accept,
                               uint16_t *d_chunk_maps, void *stream);
+
+/* The NFA variant of the classic algorithm (Sec. 2; the NFA columns of Table 3), a comparator
+ * for the RID.  The chunk automaton is the position NFA with every state initial (chunk 1: q0
+ * only); each start state q's set of active states is simulated over the chunk on its own, with no
+ * merging of runs, giving lambda_i(q) = rho(q, y_i), the set of NFA states reached (empty: q is
+ * not in PIS_i).  The join composes the chunk relations, PLAS_i = lambda_i(PLAS_{i-1}), as a tree
+ * of relation compositions on the device; the text is accepted iff PLAS_c meets F.
+ *   d_text: device pointer to len bytes; n_chunks: 1 <= c <= len (len == 0 needs c == 0).
+ *   d_sets: NULL, or a device buffer of n_chunks * n_nfa * ceil(n_nfa / 32) uint32 receiving the
+ *   rows lambda_i(q) (row (i, q) at word (i * n_nfa + q) * ceil(n_nfa / 32); bit p of its word
+ *   p / 32 = NFA state p, 0 = q0, p >= 1 = position p); chunk 1 fills only q0's row.
+ *   *h_accept = 1 if the text is in L(RE).  Synchronises `stream`.  The library allocates (and
+ * keeps, per program and device) scratch of about n_chunks * n_nfa * ceil(n_nfa / 32) * 4 bytes
+ * when d_sets is NULL.
+ * Errors: E_ARG, E_CHUNKS, E_UNSUPPORTED (more than 128 NFA states), E_NOMEM, E_CUDA. */
+int ridfa_recognize_nfa(const ridfa_program *prog, const uint8_t *d_text, size_t len, uint32_t n_chunks,
+                        uint8_t *h_accept, uint32_t *d_sets, void *stream);
 
 /* The paper has no counterpart to this call.  It is the RID path (the same reach and join
  * kernels as ridfa_recognize_async) for callers that must not allocate device memory while they

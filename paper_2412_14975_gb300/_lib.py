@@ -263,6 +263,20 @@ def ridfa_recognize_dfa_async(prog, d_text, length, n_chunks, d_accept, tuning=N
                      length, n_chunks, d_accept, tuning, d_chunk_maps, stream)
 
 
+_decl("ridfa_recognize_nfa", _c.c_int, [_vp, _vp, _c.c_size_t, _u32, _c.POINTER(_c.c_uint8), _vp, _vp])
+
+
+def ridfa_recognize_nfa(prog, d_text, length, n_chunks, d_sets=None, stream=None):
+    """Accept bit by the NFA variant of the classic algorithm (every position-NFA state a start
+    state, sets simulated per start); d_sets optionally receives the chunk relations as
+    [n_chunks][n_nfa][ceil(n_nfa / 32)] uint32 bitsets.  Synchronises the stream."""
+    acc = _c.c_uint8(0)
+    _check(_lib.ridfa_recognize_nfa(prog, _ptr(d_text) if length else None, int(length), int(n_chunks),
+                                    _c.byref(acc), _ptr(d_sets) if d_sets is not None else None, _stream(stream)),
+           "ridfa_recognize_nfa")
+    return bool(acc.value)
+
+
 def ridfa_last_status(prog, stream=None):
     code = _lib.ridfa_last_status(prog, _stream(stream))
     return code
@@ -551,15 +565,17 @@ _decl("ridfa_count_transitions", _c.c_int, [_vp, _c.c_int, _vp, _c.c_size_t, _u3
                                             _c.POINTER(TransitionCounts)])
 
 
-def ridfa_count_transitions(prog, text, n_chunks, dfa=False, n_threads=0):
+def ridfa_count_transitions(prog, text, n_chunks, dfa=False, n_threads=0, nfa=False):
     """Host transition counts of the reach phase over a host text (bytes or uint8 array):
-    dict with w_paper, w_conv, runs, dead_runs."""
+    dict with w_paper, w_conv, runs, dead_runs; dfa=True for the all-states DFA comparator,
+    nfa=True for the NFA variant."""
     if isinstance(text, (bytes, bytearray)):
         buf = np.frombuffer(text, dtype=np.uint8)
     else:
         buf = np.ascontiguousarray(text, dtype=np.uint8)
     out = TransitionCounts()
-    _check(_lib.ridfa_count_transitions(prog, int(bool(dfa)), buf.ctypes.data if buf.size else None, buf.size,
+    which = 2 if nfa else int(bool(dfa))
+    _check(_lib.ridfa_count_transitions(prog, which, buf.ctypes.data if buf.size else None, buf.size,
                                         int(n_chunks), int(n_threads), _c.byref(out)), "ridfa_count_transitions")
     return {f: getattr(out, f) for f, _ in out._fields_}
 

@@ -387,6 +387,23 @@ ClassNfa make_class_nfa(const PositionBuilder &pb, const Frag &root) {
     return N;
 }
 
+// The NFA variant's tables (32-bit words), for automata of at most 128 NFA states.
+void keep_nfa(const ClassNfa &N, ridfa::HostNfa &out) {
+    out = ridfa::HostNfa{};
+    if (N.n > 128) return;
+    const uint32_t nw = (N.n + 31) / 32;
+    auto words32 = [&](const uint64_t *r, std::vector<uint32_t> &dst) {
+        for (uint32_t w = 0; w < nw; ++w) dst.push_back(static_cast<uint32_t>(r[w / 2] >> (32 * (w & 1))));
+    };
+    out.n = N.n;
+    out.nw = nw;
+    out.n_classes = N.n_classes;
+    out.classmap = N.classmap;
+    for (uint32_t q = 0; q < N.n; ++q) words32(N.follow.row(q), out.follow);
+    for (uint32_t c = 0; c < N.n_classes; ++c) words32(N.cls.row(c), out.cls);
+    words32(N.finals.data(), out.finals);
+}
+
 // A subset automaton under construction: subsets, transitions by class (kDeadTmp = none).
 constexpr uint32_t kDeadTmp = 0xFFFFFFFFu;
 
@@ -703,6 +720,7 @@ extern "C" int ridfa_compile(const char *re, size_t re_len, const ridfa_compile_
         Frag f = pb.build(root);
         ClassNfa N = make_class_nfa(pb, f);
         if (N.n > cap) throw TooManyStates("more NFA states than the cap");
+        keep_nfa(N, P->nfa);
         build_rid(N, cap, o.minimize_interface != 0, *P);
         P->has_dfa = o.build_dfa ? build_min_dfa(N, cap, *P) : false;
     } catch (const SyntaxError &) {

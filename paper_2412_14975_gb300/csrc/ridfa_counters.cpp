@@ -81,13 +81,56 @@ void count_range(const HostAutomaton &H, const uint8_t *text, uint64_t len, uint
     *out = k;
 }
 
+// The NFA variant (Sec. 2): chunk 1 from q0, the others from every NFA state, each start's set of
+// active states followed on its own.  A step from the set S on a byte of class c executes
+// sum over q in S of |Follow(q) n cls(c)| transitions (w_paper) and processes |S| states (w_conv).
+void count_range_nfa(const HostNfa &N, const uint8_t *text, uint64_t len, uint64_t c, uint64_t c_lo,
+                     uint64_t c_hi, Counts *out) {
+    const uint32_t nw = N.nw;
+    Counts k;
+    std::vector<uint32_t> S(nw), F(nw);
+    for (uint64_t i = c_lo; i < c_hi; ++i) {
+        const uint64_t b = chunk_at(i, len, c), e = chunk_at(i + 1, len, c);
+        const uint32_t starts = i == 0 ? 1 : N.n;
+        for (uint32_t q0 = 0; q0 < starts; ++q0) {
+            std::fill(S.begin(), S.end(), 0u);
+            S[q0 >> 5] = 1u << (q0 & 31);
+            ++k.runs;
+            bool alive = true;
+            for (uint64_t p = b; p < e; ++p) {
+                const uint32_t *cm = N.cls.data() + static_cast<size_t>(N.classmap[text[p]]) * nw;
+                std::fill(F.begin(), F.end(), 0u);
+                for (uint32_t w = 0; w < nw; ++w)
+                    for (uint32_t m = S[w]; m; m &= m - 1) {
+                        const uint32_t q = 32 * w + static_cast<uint32_t>(__builtin_ctz(m));
+                        ++k.w_conv;
+                        const uint32_t *f = N.follow.data() + static_cast<size_t>(q) * nw;
+                        for (uint32_t v = 0; v < nw; ++v) {
+                            F[v] |= f[v];
+                            k.w_paper += static_cast<uint64_t>(__builtin_popcount(f[v] & cm[v]));
+                        }
+                    }
+                uint32_t any = 0;
+                for (uint32_t v = 0; v < nw; ++v) any |= (S[v] = F[v] & cm[v]);
+                if (!any) {
+                    alive = false;
+                    break;
+                }
+            }
+            if (!alive) ++k.dead;
+        }
+    }
+    *out = k;
+}
+
 }  // namespace
 }  // namespace ridfa
 
 extern "C" int ridfa_count_transitions(const ridfa_program *prog, int which, const uint8_t *h_text, size_t len,
                                        uint32_t n_chunks, uint32_t n_threads, ridfa_transition_counts *out) {
-    if (!prog || !out || (len && !h_text) || (which != 0 && which != 1)) return RIDFA_E_ARG;
+    if (!prog || !out || (len && !h_text) || which < 0 || which > 2) return RIDFA_E_ARG;
     if (which == 1 && !prog->has_dfa) return RIDFA_E_NO_DFA;
+    if (which == 2 && prog->nfa.n == 0) return RIDFA_E_UNSUPPORTED;
     if (n_chunks == 0 || n_chunks > len) return RIDFA_E_CHUNKS;
     const ridfa::HostAutomaton &H = which ? prog->dfa : prog->rid;
     uint32_t T = n_threads ? n_threads : std::max(1u, std::thread::hardware_concurrency());
@@ -97,13 +140,18 @@ extern "C" int ridfa_count_transitions(const ridfa_program *prog, int which, con
     const uint64_t c = n_chunks;
     try {
         for (uint32_t t = 1; t < T; ++t)
-            th.emplace_back(ridfa::count_range, std::cref(H), h_text, static_cast<uint64_t>(len), c, c * t / T,
-                            c * (t + 1) / T, &parts[t]);
+            if (which == 2)
+                th.emplace_back(ridfa::count_range_nfa, std::cref(prog->nfa), h_text, static_cast<uint64_t>(len), c,
+                                c * t / T, c * (t + 1) / T, &parts[t]);
+            else
+                th.emplace_back(ridfa::count_range, std::cref(H), h_text, static_cast<uint64_t>(len), c, c * t / T,
+                                c * (t + 1) / T, &parts[t]);
     } catch (...) {
         for (auto &x : th) x.join();
         return RIDFA_E_NOMEM;
     }
-    ridfa::count_range(H, h_text, len, c, 0, c / T, &parts[0]);
+    if (which == 2) ridfa::count_range_nfa(prog->nfa, h_text, len, c, 0, c / T, &parts[0]);
+    else ridfa::count_range(H, h_text, len, c, 0, c / T, &parts[0]);
     for (auto &x : th) x.join();
     ridfa_transition_counts r{};
     for (const auto &p : parts) {

@@ -1229,6 +1229,7 @@ void release_device(const ridfa_program *P) {
         cudaSetDevice(dev);
         cudaFree(ptr);
     };
+    release_nfa(P);
     for (auto &d : P->dev_rid) free_on(d.device, d.trans);
     for (auto &d : P->dev_dfa) free_on(d.device, d.trans);
     for (auto &s : P->scratch) {

@@ -51,6 +51,29 @@ struct DeviceAutomaton {
     size_t bytes = 0;
 };
 
+// The position NFA over byte classes, for the NFA variant of the classic algorithm (the
+// comparator of Sec. 2 / Table 3): follow rows, class rows (positions reading the class) and the
+// final set as bitsets of nw 32-bit words (bit q of word q / 32 = NFA state q; 0 = q0).  Kept
+// only when n <= 128 (nw <= 4); n = 0 otherwise.
+struct HostNfa {
+    uint32_t n = 0, nw = 0, n_classes = 0;
+    std::vector<uint8_t> classmap;    // [256]
+    std::vector<uint32_t> follow;     // [n][nw]
+    std::vector<uint32_t> cls;        // [n_classes][nw]
+    std::vector<uint32_t> finals;     // [nw]
+};
+
+// Device copy of a HostNfa (one per device it was uploaded to): one allocation.
+struct DeviceNfa {
+    int device = -1;
+    void *base = nullptr;
+    const uint8_t *classmap = nullptr;
+    const uint32_t *follow = nullptr, *cls = nullptr, *finals = nullptr;
+    void *scratch = nullptr;          // the call's relations (grown on demand)
+    size_t scratch_bytes = 0;
+    uint8_t *h_accept_pinned = nullptr;
+};
+
 // Per-device scratch of a program: chunk maps when the caller passes none, per-chunk summaries,
 // the join's partial products, a block ticket, the status word and the accept byte.
 struct DeviceScratch {
@@ -74,14 +97,17 @@ struct ridfa_program {
     ridfa::HostAutomaton rid;
     ridfa::HostAutomaton dfa;
     bool has_dfa = false;
+    ridfa::HostNfa nfa;                               // the NFA variant's tables (n <= 128)
     // device side (filled lazily by the device code)
     mutable std::mutex mu;
     mutable std::vector<ridfa::DeviceAutomaton> dev_rid, dev_dfa;
     mutable std::vector<ridfa::DeviceScratch> scratch;
+    mutable std::vector<ridfa::DeviceNfa> dev_nfa;
 };
 
 namespace ridfa {
 void release_device(const ridfa_program *prog);   // defined in the device code
+void release_nfa(const ridfa_program *prog);      // ridfa_nfa.cu
 
 // Device buffers supplied by the caller of launch_with_buffers: the automaton's tables and every
 // piece of scratch the reach and join kernels use.  Nothing is allocated by the launch.

@@ -124,3 +124,51 @@ def test_counter_errors():
     with pytest.raises(lib.RidfaError) as e:
         lib.ridfa_count_transitions(p, b"ab", 1, dfa=True)
     assert e.value.code == -10
+
+
+def nfa_variant_counts(nfa, chunks):
+    """The NFA variant's work (Sec. 2) written out: chunk 1 from q0, the others from every NFA
+    state, each start's set followed on its own; a step from S executes sum |rho(q, b)| transitions
+    and processes |S| states."""
+    wp = wc = runs = dead = 0
+    for i, y in enumerate(chunks):
+        for q in ([nfa.q0] if i == 0 else range(nfa.n)):
+            S = {q}
+            runs += 1
+            for b in y:
+                T = set()
+                for s in S:
+                    wc += 1
+                    t = nfa.rho(s, b)
+                    wp += len(t)
+                    T |= t
+                S = T
+                if not S:
+                    dead += 1
+                    break
+    return dict(w_paper=wp, w_conv=wc, runs=runs, dead_runs=dead)
+
+
+@pytest.mark.parametrize("re_name", ["c1", "c3", "regexp3", "codon"])
+def test_nfa_variant_counts_match_definition(re_name):
+    re_src = {"c1": textgen.C1_RE, "c3": textgen.C3_RE, "regexp3": textgen.regexp_family_re(3),
+              "codon": textgen.C2_RE.replace("{20,60}", "{2,4}")}[re_name]
+    x = {"c1": lambda: textgen.c1_text(2500, seed=11), "c3": lambda: textgen.c3_text(2500, seed=12),
+         "regexp3": lambda: textgen.regexp_family_text(2500, seed=13),
+         "codon": lambda: textgen.c2_text(2500, seed=14)}[re_name]()
+    y, _ = textgen.mutate(x, seed=15, n_subs=2)
+    prog = lib.ridfa_compile(re_src, build_dfa=False)
+    nfa = RidOracle(re_src, with_dfa=False).nfa
+    for t in (x, y):
+        for c in (1, 3, 40):
+            b = chunk_boundaries(t.size, c)
+            chunks = [bytes(t[b[i]:b[i + 1]]) for i in range(c)]
+            assert lib.ridfa_count_transitions(prog, t, c, nfa=True) == nfa_variant_counts(nfa, chunks)
+
+
+def test_nfa_variant_counts_refuse_large_nfa():
+    prog = lib.ridfa_compile(textgen.C3_RE_ANYFIELD, build_dfa=False)   # 129 NFA states
+    assert prog.info["n_nfa"] > 128
+    with pytest.raises(lib.RidfaError) as e:
+        lib.ridfa_count_transitions(prog, textgen.c3_text(1000, seed=16), 4, nfa=True)
+    assert e.value.code == -9          # E_UNSUPPORTED
