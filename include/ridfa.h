@@ -108,8 +108,11 @@ typedef struct {
                                  only); 8 two-byte steps: lane-replicated 16-bit entries for every
                                  pair of classes beside the single classes, so the converged runs
                                  take one transition lookup per two bytes (small automata:
-                                 (P/2 + 1) * (C*C + C) <= 511; text paths 1 and 3 only) (E_ARG if
-                                 the chosen layout does not fit) */
+                                 (P/2 + 1) * (C*C + C) <= 511; text paths 1 and 3 only); 9
+                                 two-byte steps in one compact table of premultiplied 16-bit
+                                 offsets (pair and single columns), a lane's runs sharing each
+                                 pair's column ((P + 1) * (C*C + C) <= 32767; text paths 1 and 5
+                                 only) (E_ARG if the chosen layout does not fit) */
     uint32_t text_path;       /* how the converged runs read the text: 0 auto; 1 each lane's own
                                  16-byte global loads; 2 retired (per-lane bulk copies; E_ARG);
                                  3 warp-cooperative coalesced loads staged in shared memory; 4

@@ -815,6 +815,7 @@ cudaError_t piece_dispatch(const ReachArgs &a, const ReachPlan &pl, int sms, cud
         case kModeRep16x4: return piece_r<LutRep16x4>(pl.R, a, grid, smem, pl.tis, st);
         case kModeRep16x4C: return piece_r<LutRep16x4C>(pl.R, a, grid, smem, pl.tis, st);
         case kModePair: return piece_r<LutPair>(pl.R, a, grid, smem, pl.tis, st);
+        case kModePairC: return piece_r<LutPairC>(pl.R, a, grid, smem, pl.tis, st);
         case kModePlain: return piece_r<LutPlain>(pl.R, a, grid, smem, pl.tis, st);
         default: return piece_r<LutFlat>(pl.R, a, grid, smem, pl.tis, st);
     }
@@ -860,12 +861,14 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // slower -- its gathers conflict less, but its larger footprint leaves fewer warps and the
     // time goes to run imbalance, not conflicts)
     const size_t plain = LutPlain::smem_bytes(A), flat = LutFlat::smem_bytes(A), rep16x4 = LutRep16x4::smem_bytes(A),
-                 rep16x4c = LutRep16x4C::smem_bytes(A), pair = LutPair::smem_bytes(A);
+                 rep16x4c = LutRep16x4C::smem_bytes(A), pair = LutPair::smem_bytes(A),
+                 pairc = LutPairC::smem_bytes(A);
     const bool ok16 = LutRep<true>::fits16(A) && rep16 <= limit, ok32 = rep32 <= limit,
                okp = LutPart::fits(A) && part16 <= limit, okplain = LutPlain::fits(A) && plain <= limit,
                ok16x4 = LutRep16x4::fits(A) && rep16x4 <= limit,
                ok16x4c = LutRep16x4C::fits(A) && rep16x4c + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit,
-               okpair = LutPair::fits(A) && pair + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit;
+               okpair = LutPair::fits(A) && pair + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit,
+               okpairc = LutPairC::fits(A) && pairc + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit;
     // replicated layouts that leave room for at least 16 warps' staging come first; a 32-bit table
     // that leaves fewer is taken only when no scaled 16-bit one fits (measured: a 6-warp 32-bit
     // table ran at a third of the speed of a 26-warp scaled one)
@@ -895,19 +898,29 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
         if (allow_pair && okpair && (tp == 0 || tp == 1 || tp == 3) &&
             pair + 32 * static_cast<size_t>(kWarpCoopBytes) <= limit)
             mode = kModePair;
+        // automata left with the compact table (runs that stay apart, several to a lane on the
+        // set path) take its two-byte form where it fits beside a full set-path block: a lane's
+        // runs then share each pair's column and pay half the transition lookups (the codon RE
+        // on 1 GiB, 65,536 chunks: 1,057 -> 1,256 GB/s; on the regexp family, whose replicated
+        // tables keep one run a lane, the two-byte compact table measured 16 % slower)
+        if (allow_pair && mode == kModePlain && okplain && okpairc && (tp == 0 || tp == 1 || tp == 5) &&
+            pairc + 16 * static_cast<size_t>(kWarpCoopBytes) <= limit)
+            mode = kModePairC;
     }
     if (mode == kModeRep16x4 && !ok16x4) return RIDFA_E_ARG;
     if (mode == kModeRep16x4C && !ok16x4c) return RIDFA_E_ARG;
     if (mode == kModePair && !okpair) return RIDFA_E_ARG;
+    if (mode == kModePairC && !okpairc) return RIDFA_E_ARG;
     if (mode == kModePlain && !okplain) mode = kModeFlat;    // the compact table, through generic loads
     if ((mode == kModeRep16 && !ok16) || (mode == kModeRep32 && !ok32) || (mode == kModePart16 && !okp))
         return RIDFA_E_ARG;
-    if (mode < kModePlain || mode > kModePair) return RIDFA_E_ARG;
+    if (mode < kModePlain || mode > kModePairC) return RIDFA_E_ARG;
     pl.mode = mode;
     pl.tis = (mode == kModeFlat && flat <= limit) ? 1 : 0;
     const size_t table_smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : mode == kModePart16 ? part16
                               : mode == kModeRep16x4 ? rep16x4 : mode == kModeRep16x4C ? rep16x4c
-                              : mode == kModePair ? pair : mode == kModePlain ? plain : (pl.tis ? flat : 256);
+                              : mode == kModePair ? pair : mode == kModePairC ? pairc
+                              : mode == kModePlain ? plain : (pl.tis ? flat : 256);
     const int cap = pl.R <= 4 ? 1024 : 512;
     const uint32_t text_path = tuning ? tuning->text_path : 0;
     if (text_path > 5) return RIDFA_E_ARG;
@@ -932,7 +945,7 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // Automata whose table is too large to replicate are the ones whose runs stay apart: there a
     // lane finishes all of its chunk's runs together (measured on the codon RE: 1.21x; on
     // replicated-table workloads the 512-thread cap of that variant cost 8-13%).
-    const bool many_runs = mode == kModePlain || mode == kModeFlat || mode == kModeRep16x4C;
+    const bool many_runs = mode == kModePlain || mode == kModeFlat || mode == kModeRep16x4C || mode == kModePairC;
     if (text_path == 0)
         pl.path = !aligned ? kPathGlobal
                   : !w_coop ? kPathGlobal
@@ -949,6 +962,7 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // for the single-run cooperative path (and plain global loads)
     if (mode == kModeRep16x4C && pl.path != kPathCoopSet && pl.path != kPathGlobal) return RIDFA_E_ARG;
     if (mode == kModePair && pl.path != kPathCoop && pl.path != kPathGlobal) return RIDFA_E_ARG;
+    if (mode == kModePairC && pl.path != kPathCoopSet && pl.path != kPathGlobal) return RIDFA_E_ARG;
     const int warps_fit = pl.path == kPathCoop      ? w_coop
                           : pl.path == kPathCoopSet ? w_set
                           : pl.path == kPathCoop2 ? w_coop2

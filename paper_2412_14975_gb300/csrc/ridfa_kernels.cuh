@@ -379,8 +379,64 @@ struct LutPair {
     __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
     __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
     __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return lds_u16(lt1 + s + c); }
+    // the pair column of classes (c1, c2), shared by every run stepping the same two bytes
+    __device__ __forceinline__ uint32_t pair_col(uint32_t c1, uint32_t c2) const { return c1 * C + c2; }
+    __device__ __forceinline__ uint32_t next_pc(uint32_t s, uint32_t pc) const { return lds_u16(lt + s + pc); }
     __device__ __forceinline__ uint32_t next2(uint32_t s, uint32_t c1, uint32_t c2) const {
-        return lds_u16(lt + s + (c1 * C + c2));
+        return next_pc(s, pair_col(c1, c2));
+    }
+};
+
+// Two-byte transitions in one compact table, for automata whose runs stay apart (the set path,
+// where a lane steps all of its chunk's runs over the same bytes): row s holds NP = C*C + C 16-bit
+// entries, the C*C pair columns (c1, c2) -> delta(delta(s, c1), c2) and then the C single columns,
+// each entry the premultiplied row offset 2*NP*s' of its target, so
+//   pair step   s' = T[s + 2*(c1*C + c2)]   (the column shared by all of a lane's runs),
+//   single step s' = T[s + 2*C*C + 2*c].
+// The class table is lane-replicated (word b*32 + l = 2*class(b), conflict-free).  A lane with m
+// runs then pays 1 class lookup per byte and m/2 transition lookups instead of m; the gathers
+// into the table can share banks, as in Plain.  Needs 2*NP*(P+1) <= 64 KiB.
+struct LutPairC {
+    static constexpr bool kPairs = true;
+    uint32_t lc, bt, bt1;     // this lane's class copy; the table (pairs, singles)
+    uint32_t C, row;          // row: 2*NP bytes per state
+    static uint32_t np_of(const Automaton &A) { return A.C * A.C + A.C; }
+    static size_t smem_bytes(const Automaton &A) {
+        return 256 * 128 + static_cast<size_t>(A.n + 1) * np_of(A) * 2;
+    }
+    static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n + 1) * np_of(A) * 2 <= 0xFFFF; }
+    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+        C = A.C;
+        const uint32_t NP = C * C + C;
+        row = 2 * NP;
+        const uint32_t base_c = smem_addr(smem);
+        bt = base_c + 256 * 128;
+        bt1 = bt + 2 * C * C;
+        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) sts_u32(base_c + i * 4, 2u * A.classmap[i >> 5]);
+        const uint32_t n = A.n;               // the dead state: row n maps to itself
+        auto value = [&](uint32_t e) -> uint32_t {
+            const uint32_t st = e / NP, col = e % NP;
+            const uint32_t t = col < C * C ? A.trans[A.trans[st * C + col / C] * C + col % C]
+                                           : A.trans[st * C + col - C * C];
+            return t * row;
+        };
+        const uint32_t cnt = (n + 1) * NP;
+        for (uint32_t i = threadIdx.x; i < (cnt + 1) / 2; i += blockDim.x) {
+            const uint32_t v0 = value(2 * i);
+            const uint32_t v1 = 2 * i + 1 < cnt ? value(2 * i + 1) : 0u;
+            sts_u32(bt + i * 4, v0 | (v1 << 16));
+        }
+        lc = base_c + (threadIdx.x & 31) * 4;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return id * row; }
+    __device__ __forceinline__ uint32_t id(uint32_t s) const { return s / row; }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return lds_u16(bt1 + s + c); }
+    __device__ __forceinline__ uint32_t pair_col(uint32_t c1, uint32_t c2) const { return c1 * C + c2; }
+    __device__ __forceinline__ uint32_t next_pc(uint32_t s, uint32_t pc) const { return lds_u16(bt + s + pc); }
+    __device__ __forceinline__ uint32_t next2(uint32_t s, uint32_t c1, uint32_t c2) const {
+        return next_pc(s, pair_col(c1, c2));
     }
 };
 
@@ -781,10 +837,19 @@ __device__ __forceinline__ void set_window(const LUT &T, uint32_t sb, uint32_t s
             uint32_t cl[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) cl[q] = T.cls_at(w[q >> 2], q & 3);
+            if constexpr (has_pairs<LUT>::value) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+                for (int q = 0; q < 16; q += 2) {
+                    const uint32_t pc = T.pair_col(cl[q], cl[q + 1]);
 #pragma unroll
-                for (int g = 0; g < M; ++g) s[g] = T.next(s[g], cl[q]);
+                    for (int g = 0; g < M; ++g) s[g] = T.next_pc(s[g], pc);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+#pragma unroll
+                    for (int g = 0; g < M; ++g) s[g] = T.next(s[g], cl[q]);
+            }
         }
     } else {
         for (uint32_t o = o0; o < o1; ++o) {

@@ -11,7 +11,7 @@ namespace ridfa {
 
 // table layouts (ridfa_tuning::table_mode)
 enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3, kModePart16 = 4, kModeFlat = 5,
-                       kModeRep16x4 = 6, kModeRep16x4C = 7, kModePair = 8 };
+                       kModeRep16x4 = 6, kModeRep16x4C = 7, kModePair = 8, kModePairC = 9 };
 
 // How one reach launch is laid out: table layout, text path, block/grid, shared memory.
 struct ReachPlan {
@@ -463,6 +463,10 @@ cudaError_t reach_m(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, in
         case kModePair:
             // (two-byte steps serve the single-run cooperative path and plain global loads)
             if constexpr (PATH == kPathCoop || PATH == kPathGlobal) return reach_r<LutPair, PATH>(a, pl, st, per_sm);
+            else return cudaErrorInvalidValue;
+        case kModePairC:
+            // (the compact two-byte table serves the set path and plain global loads)
+            if constexpr (PATH == kPathCoopSet || PATH == kPathGlobal) return reach_r<LutPairC, PATH>(a, pl, st, per_sm);
             else return cudaErrorInvalidValue;
         case kModePlain: return reach_r<LutPlain, PATH>(a, pl, st, per_sm);
         default: return reach_r<LutFlat, PATH>(a, pl, st, per_sm);

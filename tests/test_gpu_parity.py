@@ -258,7 +258,8 @@ def test_tuning_variants_agree(mode):
     re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
     z = textgen.c2_text(1 << 16, seed=79)
     # 424 states x 5 classes: the 16-bit offsets overflow and the 32-bit replicated table exceeds
-    # shared memory; the compact table (automatic) and the half-replicated one (on request) fit
+    # shared memory; the compact tables (the two-byte one automatic) and the half-replicated one
+    # (on request) fit
     check(re2, z, 200, tuning=dict(table_mode=mode if mode in (1, 4, 5, 6) else 0), dfa_too=False)
     check(re2, z, 1000, tuning=dict(table_mode=mode if mode in (1, 4, 5, 6) else 0, text_path=1), dfa_too=False)
     prog = lib.ridfa_compile(re2)
@@ -491,6 +492,51 @@ def test_compact_class_table_layout():
         with pytest.raises(lib.RidfaError) as e:
             lib.ridfa_recognize(prog, to_device(x), x.size, 1000, tuning=dict(table_mode=7, text_path=tp))
         assert e.value.code == -1
+
+
+def test_compact_two_byte_layout():
+    """Table layout 9 (two-byte steps in one compact table: a lane's runs share each pair's
+    column; single steps at ragged edges and hand-off positions): every row equals the oracle's
+    on the codon RE (several runs per lane on the set path), the regexp family and the C1 RE,
+    aligned (set path) and unaligned (global loads) texts, bytes outside the alphabet, few chunks
+    (lockstep pieces and look-back start sets); automata whose pair table does not fit, and the
+    single-run cooperative paths, refuse it."""
+    re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
+    x = textgen.c2_text((1 << 20) + 13, seed=401)
+    for c in (1, 1000, 3001):
+        check(re2, x, c, dfa_too=False, rows=list(range(c)), tuning=dict(table_mode=9))
+    check(re2, x, 1000, dfa_too=False, rows=list(range(1000)), tuning=dict(table_mode=9, text_path=1))
+    check(re2, x, 1000, dfa_too=False, rows=list(range(1000)), tuning=dict(table_mode=9, text_path=5))
+    y, _ = textgen.mutate(x, seed=402, n_subs=5, alphabet=b"ACGTN")
+    check(re2, y, 777, dfa_too=False, rows=list(range(777)), tuning=dict(table_mode=9))
+    check(re2, x, 2, dfa_too=False, tuning=dict(table_mode=9))          # look-back pieces
+    for re_src, z in ((textgen.regexp_family_re(7), textgen.regexp_family_text((1 << 18) + 5, seed=403)),
+                      (textgen.C1_RE, textgen.c1_text((1 << 17) + 3, seed=404))):
+        for c in (4, 1000, 4099):
+            check(re_src, z, c, rows=list(range(c)) if c <= 1000 else None, tuning=dict(table_mode=9))
+        w, _ = textgen.mutate(z, seed=405, n_subs=3, alphabet=b"ACGTabN\n")
+        check(re_src, w, 1000, rows=list(range(1000)), tuning=dict(table_mode=9))
+    prog = lib.ridfa_compile(re2)
+    o, ser = oracle(re2)
+    base = torch.from_numpy(np.concatenate([np.zeros(16, np.uint8), x])).to("cuda:0")
+    z = x[7:]
+    maps = torch.empty((500, prog.info["k"]), dtype=torch.int16, device="cuda:0")
+    acc = lib.ridfa_recognize(prog, base[16 + 7:], z.size, 500, tuning=dict(table_mode=9), d_chunk_maps=maps)
+    assert acc == ser.accepts(z)
+    got = maps.cpu().numpy().view(np.uint16)
+    want = o.lambda_rows(z, 500, [0, 1, 250, 498, 499])
+    for i in want:
+        assert np.array_equal(got[i], want[i])
+    for tp in (3, 4):
+        with pytest.raises(lib.RidfaError) as e:
+            lib.ridfa_recognize(prog, to_device(x), x.size, 1000, tuning=dict(table_mode=9, text_path=tp))
+        assert e.value.code == -1
+    # the codon RE {3,6}: 1,588 states x 30 columns do not fit 16-bit row offsets
+    prog = lib.ridfa_compile(textgen.C2_RE.replace("{20,60}", "{3,6}"))
+    assert (prog.info["n_states"] + 1) * 30 * 2 > 0xFFFF
+    with pytest.raises(lib.RidfaError) as e:
+        lib.ridfa_recognize(prog, to_device(x), x.size, 100, tuning=dict(table_mode=9))
+    assert e.value.code == -1
 
 
 def test_two_byte_step_layout():
