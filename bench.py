@@ -176,6 +176,30 @@ def cpu_baseline(name, re_src, budget_s=12.0, seed=7):
                       f"state-set simulation pass ({dt:.1f} s)"}
 
 
+def measure_cpu_context(lib, prog, hx, acc, has_dfa, serial_cap=1 << 30):
+    """The recognition on the host's cores (ridfa_cpu_recognize): the serial table loop on a
+    prefix of at most serial_cap bytes, and one chunk per hardware thread over the whole text,
+    RID and all-states DFA; GB/s of one timed pass each."""
+    threads = os.cpu_count() or 1
+    pre = hx[:min(hx.size, serial_cap)]
+    out = {"unit": "GB/s", "threads": threads, "serial_sample_bytes": int(pre.size),
+           "chunked_bytes": int(hx.size), "chunks": threads}
+
+    def rate(x, c, t, dfa):
+        t0 = time.perf_counter()
+        a = lib.ridfa_cpu_recognize(prog, x, c, dfa=dfa, n_threads=t)
+        return a, round(x.size / (time.perf_counter() - t0) / 1e9, 3)
+
+    _, out["serial_rid"] = rate(pre, 1, 1, False)
+    a, out["chunked_rid"] = rate(hx, threads, threads, False)
+    assert a == acc, "host and device recognition disagree"
+    if has_dfa:
+        _, out["serial_dfa"] = rate(pre, 1, 1, True)
+        a, out["chunked_dfa"] = rate(hx, threads, threads, True)
+        assert a == acc, "host all-states DFA and device recognition disagree"
+    return out
+
+
 def run_reference_multi(args, name):
     """The oracle on the batched or served workload: a bounded sample of its texts, item by item.
     (The workload's random REs are selected with the library's host compiler; the timed path is
@@ -578,6 +602,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dfa", action="store_true")
     ap.add_argument("--no-counts", action="store_true", help="skip the host transition counters")
+    ap.add_argument("--no-cpu-context", action="store_true",
+                    help="skip the host recognition (serial table loop, chunks on all host threads)")
     ap.add_argument("--nfa", action="store_true",
                     help="also time the NFA variant of the classic algorithm (Sec. 2) on the same text "
                          "and count its transitions (Table 3's NFA columns)")
@@ -807,6 +833,12 @@ def main():
         hbm_text_rate = peaks["hbm_gbs"] * n / alg_bytes
         roofline["binding"] = "smem_lookups" if lut_text_rate < hbm_text_rate else "hbm"
         roofline["binding_frac"] = round(text_rate / min(lut_text_rate, hbm_text_rate), 4)
+    # the paper's own setting for context: the same recognition on the host's cores through the
+    # library's host entry point (serial table loop; one chunk per hardware thread)
+    cpu_context = None
+    if rank == 0 and world == 1 and not args.no_cpu_context:
+        hx = h_text.numpy() if not args.no_e2e else d_text.cpu().numpy()
+        cpu_context = measure_cpu_context(lib, prog, hx, acc, info["n_dfa_states"] > 0)
     if not args.no_e2e:
         del h_text
 
@@ -842,7 +874,8 @@ def main():
                            "chunk_autotune_GBps": autotune,
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "dfa_value": round(dfa_value, 3) if dfa_value else None,
-                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "work": work,
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+                "cpu_context": cpu_context, "work": work,
                 "interface_ablation": ablation, "nfa_variant": nfa,
                 "batched": batched, "served": served,
                 "gpu_launches": 2 * args.steps}

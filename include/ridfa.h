@@ -223,6 +223,21 @@ typedef struct {
 int ridfa_count_transitions(const ridfa_program *prog, int which, const uint8_t *h_text, size_t len,
                             uint32_t n_chunks, uint32_t n_threads, ridfa_transition_counts *out);
 
+/* The same recognition on the host's cores, the CPU context of the device numbers (the paper
+ * measures its method on the cores of one machine, Sec. 4).  n_chunks = 1: the serial recognizer,
+ * the table loop from {q0} (Sec. 2; which = 1: the classic serial run of the minimal DFA).
+ * n_chunks > 1: the chunked speculative recognition of Sec. 3.2 -- chunk 1 from {q0}'s slot, every
+ * other chunk from every interface slot, runs that meet in one state at one position merged, then
+ * the join PLAS_i = lambda_i(if_min(PLAS_{i-1})) and PLAS_c n F^RID != {} -- with the chunks split
+ * over n_threads host threads (0 = all hardware threads) and the join on the calling thread;
+ * which = 1: the all-states DFA variant (Sec. 2).  Chunk boundaries as on the device.  h_text:
+ * host pointer to len bytes; len == 0 needs n_chunks == 0 (the answer is whether the empty word
+ * is in L).  *h_accept = 1 if text in L(RE) else 0.  ridfa_recognize never calls this (no host
+ * fallback exists); it holds c * k uint16 chunk maps in host memory while it runs.
+ * Errors: E_ARG, E_NO_DFA, E_CHUNKS, E_NOMEM. */
+int ridfa_cpu_recognize(const ridfa_program *prog, int which, const uint8_t *h_text, size_t len,
+                        uint32_t n_chunks, uint32_t n_threads, uint8_t *h_accept);
+
 /* Recognize one text resident on the device (the RID: reach + join, Sec. 3.2).
  * d_text: device pointer to len bytes (any alignment).  n_chunks: c, 1 <= c <= len.
  * len == 0 is allowed with n_chunks == 0: the answer is whether the empty word is in L.

@@ -17,5 +17,5 @@ from ._lib import (RIDFA_MAX_SLOTS, RIDFA_MAX_STATES, RIDFA_NOALLOC_SCRATCH_BYTE
                    ridfa_recognize_async, ridfa_recognize_dfa, ridfa_recognize_dfa_async, ridfa_recognize_nfa, ridfa_recognize_host, ridfa_check_bounded_wait,
                    ridfa_slots, ridfa_state_set, ridfa_strerror,
                    Batch, ridfa_batch_create, ridfa_batch_run, ridfa_batch_get_stats, ridfa_batch_free,
-                   ridfa_recognize_batch, Server, RIDFA_SUBMIT_DEVICE_TEXT, ridfa_count_transitions,
+                   ridfa_recognize_batch, Server, RIDFA_SUBMIT_DEVICE_TEXT, ridfa_count_transitions, ridfa_cpu_recognize,
                    ShardSummary, ridfa_recognize_shard, ridfa_join_shards, ridfa_join_scan)

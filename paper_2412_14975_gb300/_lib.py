@@ -580,6 +580,23 @@ def ridfa_count_transitions(prog, text, n_chunks, dfa=False, n_threads=0, nfa=Fa
     return {f: getattr(out, f) for f, _ in out._fields_}
 
 
+_decl("ridfa_cpu_recognize", _c.c_int, [_vp, _c.c_int, _vp, _c.c_size_t, _u32, _u32, _c.POINTER(_c.c_uint8)])
+
+
+def ridfa_cpu_recognize(prog, text, n_chunks, dfa=False, n_threads=0):
+    """The recognition on the host's cores (a comparison, never a fallback): n_chunks = 1 is
+    the serial table loop, n_chunks > 1 the chunked speculative run on n_threads threads (0 =
+    all); dfa=True for the all-states DFA variant.  Returns the accept bit."""
+    if isinstance(text, (bytes, bytearray)):
+        buf = np.frombuffer(text, dtype=np.uint8)
+    else:
+        buf = np.ascontiguousarray(text, dtype=np.uint8)
+    acc = _c.c_uint8(0)
+    _check(_lib.ridfa_cpu_recognize(prog, int(bool(dfa)), buf.ctypes.data if buf.size else None, buf.size,
+                                    int(n_chunks), int(n_threads), _c.byref(acc)), "ridfa_cpu_recognize")
+    return bool(acc.value)
+
+
 # ---------------------------------------------------------------------------------- shards
 class ShardSummary(_c.Structure):
     _fields_ = [("k", _u32), ("n_out", _u32), ("entry", _c.c_uint16 * RIDFA_MAX_SLOTS),
