@@ -404,6 +404,33 @@ def measure_batch(args, lib, torch, dev, stream, world, rank, steps, warmup, ora
     e1.record(stream)
     torch.cuda.synchronize()
     single_value = total / (e0.elapsed_time(e1) / 1e3) / 1e9
+    # each RE's texts end to end as one long text (every RE here is star-closed, so the
+    # concatenation of its members is a member), recognized with the batch's chunk length: the
+    # rate each RE reaches alone; the batch against the sum of those times shows what mixing
+    # programs in one graph costs or gains
+    per_re = []
+    sep_ms = 0.0
+    if not args.no_batch_per_re:
+        rid_all = [it[2] for it in items]
+        for r in range(len(progs)):
+            xs = [texts[i] for i in range(len(texts)) if rid_all[i] == r and texts[i].size]
+            if not xs:
+                continue
+            cat = np.concatenate(xs)
+            dt = torch.from_numpy(cat).to(dev)
+            c = max(1, min(cat.size, (cat.size + L - 1) // L))
+            lib.ridfa_recognize_async(progs[r], dt.data_ptr(), cat.size, c, acc1, stream=stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(3):
+                lib.ridfa_recognize_async(progs[r], dt.data_ptr(), cat.size, c, acc1, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 3
+            sep_ms += t
+            per_re.append({"re": r, "bytes": int(cat.size), "chunks": int(c), "GBps": round(cat.size / (t / 1e3) / 1e9, 1)})
+            del dt
+        torch.cuda.empty_cache()
     # accept bits of a seeded sample of items against the oracle
     rid = [it[2] for it in items]
     rng = np.random.Generator(np.random.PCG64(5))
@@ -421,6 +448,9 @@ def measure_batch(args, lib, torch, dev, stream, world, rank, steps, warmup, ora
             "ms_per_step": round(ms / steps, 4),
             "single_text_per_launch_GBps": round(single_value, 3),
             "batched_over_single": round(value / single_value, 3),
+            "per_re_alone": per_re or None,
+            "per_re_alone_GBps": round(total / (sep_ms / 1e3) / 1e9, 3) if sep_ms else None,
+            "batched_over_per_re_alone": round(value / (total / (sep_ms / 1e3) / 1e9), 3) if sep_ms else None,
             "config": {"workload": f"batched: {len(items)} texts, lognormal median 256 KiB sigma 1, "
                                    f"16 REs (3 single-text + 13 random), half mutated, one CUDA graph",
                        "total_bytes": total, "chunk_len": L, "chunks": st["total_chunks"],
@@ -443,6 +473,8 @@ def run_batch(args, lib, torch, dev, stream, world, rank):
                 "data": "synthetic", "config": r["config"],
                 "single_text_per_launch_GBps": r["single_text_per_launch_GBps"],
                 "batched_over_single": r["batched_over_single"], "oracle_check": r["oracle_check"],
+                "per_re_alone": r["per_re_alone"], "per_re_alone_GBps": r["per_re_alone_GBps"],
+                "batched_over_per_re_alone": r["batched_over_per_re_alone"],
                 "clocks": r["clocks"], "cpu_baseline": r["cpu_baseline"], "gpu_launches": r["gpu_launches"]}
         print(json.dumps(line), flush=True)
 
@@ -593,6 +625,8 @@ def main():
     ap.add_argument("--served-pool", type=int, default=2048)
     ap.add_argument("--batch-texts", type=int, default=10000)
     ap.add_argument("--batch-chunk-len", type=int, default=0, help="0 = autotune")
+    ap.add_argument("--no-batch-per-re", action="store_true",
+                    help="skip timing each batch RE alone on the concatenation of its texts")
     ap.add_argument("--text-bytes", type=int, default=None)
     ap.add_argument("--chunks", type=int, default=None)
     ap.add_argument("--seed", type=int, default=0x5EED02)

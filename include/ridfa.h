@@ -112,7 +112,11 @@ typedef struct {
                                  two-byte steps in one compact table of premultiplied 16-bit
                                  offsets (pair and single columns), a lane's runs sharing each
                                  pair's column ((P + 1) * (C*C + C) <= 32767; text paths 1 and 5
-                                 only) (E_ARG if the chosen layout does not fit) */
+                                 only); 10 two-byte steps in F lane copies (the layout of 8 with
+                                 16, 8, 4 or 2 copies, the most whose 16-bit entries fit, at most
+                                 32/F wavefronts a lookup: (P/2 + 1) * (C*C + C) * 4F <= 65535;
+                                 text paths 1 and 3 only) (E_ARG if the chosen layout does not
+                                 fit) */
     uint32_t text_path;       /* how the converged runs read the text: 0 auto; 1 each lane's own
                                  16-byte global loads; 2 retired (per-lane bulk copies; E_ARG);
                                  3 warp-cooperative coalesced loads staged in shared memory; 4

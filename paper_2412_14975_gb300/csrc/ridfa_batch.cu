@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_batch_kernel(BatchReachArg
         const ProgDesc &P = b.progs[task.prog];
         const Automaton &A = P.A;
         if (static_cast<int>(task.prog) != cur) {
-            T.setup(A, smem, P.tis != 0);
+            T.setup(A, smem, P.tis);
             __syncthreads();
             cur = static_cast<int>(task.prog);
         }

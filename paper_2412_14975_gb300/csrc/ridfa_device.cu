@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(256) rid_piece_kernel(ReachArgs p, int table_i
     extern __shared__ __align__(128) uint8_t smem[];
     const Automaton &A = p.A;
     LUT T;
-    T.setup(A, smem, table_in_smem != 0);
+    T.setup(A, smem, static_cast<uint32_t>(table_in_smem));
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t dead = T.enc(A.n);
@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(512, 1) rid_lookback_kernel(LookbackArgs p, in
     extern __shared__ __align__(128) uint8_t smem[];
     const Automaton &A = p.A;
     LUT T;
-    T.setup(A, smem, table_in_smem != 0);
+    T.setup(A, smem, static_cast<uint32_t>(table_in_smem));
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t dead = T.enc(A.n);
@@ -816,6 +816,7 @@ cudaError_t piece_dispatch(const ReachArgs &a, const ReachPlan &pl, int sms, cud
         case kModeRep16x4C: return piece_r<LutRep16x4C>(pl.R, a, grid, smem, pl.tis, st);
         case kModePair: return piece_r<LutPair>(pl.R, a, grid, smem, pl.tis, st);
         case kModePairC: return piece_r<LutPairC>(pl.R, a, grid, smem, pl.tis, st);
+        case kModePairF: return piece_r<LutPairF>(pl.R, a, grid, smem, pl.tis, st);
         case kModePlain: return piece_r<LutPlain>(pl.R, a, grid, smem, pl.tis, st);
         default: return piece_r<LutFlat>(pl.R, a, grid, smem, pl.tis, st);
     }
@@ -869,6 +870,13 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
                ok16x4c = LutRep16x4C::fits(A) && rep16x4c + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit,
                okpair = LutPair::fits(A) && pair + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit,
                okpairc = LutPairC::fits(A) && pairc + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit;
+    // the most lane copies (16, 8, 4 or 2) of the two-byte table whose entries fit 16 bits and that
+    // leave room for 16 warps' staging (0: none)
+    uint32_t pair_f = 0;
+    for (uint32_t f = 16; f >= 2 && !pair_f; f /= 2)
+        if (LutPairF::fits(A, f) && LutPairF::smem_bytes(A, f) + 16 * static_cast<size_t>(kWarpCoopBytes) <= limit)
+            pair_f = f;
+    const size_t pairf = pair_f ? LutPairF::smem_bytes(A, pair_f) : 0;
     // replicated layouts that leave room for at least 16 warps' staging come first; a 32-bit table
     // that leaves fewer is taken only when no scaled 16-bit one fits (measured: a 6-warp 32-bit
     // table ran at a third of the speed of a 26-warp scaled one)
@@ -906,20 +914,28 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
         if (allow_pair && mode == kModePlain && okplain && okpairc && (tp == 0 || tp == 1 || tp == 5) &&
             pairc + 16 * static_cast<size_t>(kWarpCoopBytes) <= limit)
             mode = kModePairC;
+        // the half-replicated one-byte table gives way to the two-byte table in as many lane
+        // copies as fit (a pair gather of at most 32/F wavefronts pays for two bytes where a
+        // half-replicated lookup costs up to 2 for one): regexp family k = 7 (8 copies) 2,200 ->
+        // 2,284 GB/s, the any-field record lines (2 copies) 2,559 -> 2,777; not where the fully
+        // replicated pair table fits (regexp k = 5: 16 copies ran 10 % slower than 32)
+        if (allow_pair && mode == kModePart16 && pair_f && (tp == 0 || tp == 1 || tp == 3))
+            mode = kModePairF;
     }
     if (mode == kModeRep16x4 && !ok16x4) return RIDFA_E_ARG;
     if (mode == kModeRep16x4C && !ok16x4c) return RIDFA_E_ARG;
     if (mode == kModePair && !okpair) return RIDFA_E_ARG;
     if (mode == kModePairC && !okpairc) return RIDFA_E_ARG;
+    if (mode == kModePairF && !pair_f) return RIDFA_E_ARG;
     if (mode == kModePlain && !okplain) mode = kModeFlat;    // the compact table, through generic loads
     if ((mode == kModeRep16 && !ok16) || (mode == kModeRep32 && !ok32) || (mode == kModePart16 && !okp))
         return RIDFA_E_ARG;
-    if (mode < kModePlain || mode > kModePairC) return RIDFA_E_ARG;
+    if (mode < kModePlain || mode > kModePairF) return RIDFA_E_ARG;
     pl.mode = mode;
-    pl.tis = (mode == kModeFlat && flat <= limit) ? 1 : 0;
+    pl.tis = mode == kModePairF ? static_cast<int>(pair_f) : (mode == kModeFlat && flat <= limit) ? 1 : 0;
     const size_t table_smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : mode == kModePart16 ? part16
                               : mode == kModeRep16x4 ? rep16x4 : mode == kModeRep16x4C ? rep16x4c
-                              : mode == kModePair ? pair : mode == kModePairC ? pairc
+                              : mode == kModePair ? pair : mode == kModePairC ? pairc : mode == kModePairF ? pairf
                               : mode == kModePlain ? plain : (pl.tis ? flat : 256);
     const int cap = pl.R <= 4 ? 1024 : 512;
     const uint32_t text_path = tuning ? tuning->text_path : 0;
@@ -963,6 +979,7 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     if (mode == kModeRep16x4C && pl.path != kPathCoopSet && pl.path != kPathGlobal) return RIDFA_E_ARG;
     if (mode == kModePair && pl.path != kPathCoop && pl.path != kPathGlobal) return RIDFA_E_ARG;
     if (mode == kModePairC && pl.path != kPathCoopSet && pl.path != kPathGlobal) return RIDFA_E_ARG;
+    if (mode == kModePairF && pl.path != kPathCoop && pl.path != kPathGlobal) return RIDFA_E_ARG;
     const int warps_fit = pl.path == kPathCoop      ? w_coop
                           : pl.path == kPathCoopSet ? w_set
                           : pl.path == kPathCoop2 ? w_coop2

@@ -172,7 +172,7 @@ struct LutPlain {
     uint32_t row;             // 2*C: bytes per state row
     static size_t smem_bytes(const Automaton &A) { return 256 * 128 + static_cast<size_t>(A.n + 1) * A.C * 2; }
     static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n + 1) * A.C * 2 <= 0xFFFF; }
-    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+    __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t) {
         row = 2 * A.C;
         const uint32_t base_c = smem_addr(smem);
         bt = base_c + 256 * 128;
@@ -199,7 +199,8 @@ struct LutFlat {
     const uint8_t *cls;
     uint32_t C;
     static size_t smem_bytes(const Automaton &A) { return 256 + static_cast<size_t>(A.n + 1) * A.C * 2; }
-    __device__ void setup(const Automaton &A, uint8_t *smem, bool table_in_smem) {
+    __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t aux) {
+        const bool table_in_smem = aux != 0;
         uint8_t *s_cls = smem;
         uint16_t *s_t = reinterpret_cast<uint16_t *>(smem + 256);
         for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_cls[i] = A.classmap[i];
@@ -238,7 +239,7 @@ struct LutRep {
     __device__ __forceinline__ uint32_t cls_off(uint32_t c) const {
         return W16 ? (c >> 1) * 128 + (c & 1) * 2 : c * 128;
     }
-    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+    __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t) {
         const uint32_t Cp = cpad(A);
         row = W16 ? Cp * 64 : Cp * 128;
         const uint32_t base_c = smem_addr(smem);
@@ -291,7 +292,7 @@ struct LutRep16x4T {
     static size_t smem_bytes(const Automaton &A) { return class_bytes() + static_cast<size_t>(A.n + 1) * cpad(A) * 64; }
     static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n) * cpad(A) * 16 <= 0xFFFF; }
     __device__ __forceinline__ static uint32_t cls_off(uint32_t c) { return (c >> 1) * 128 + (c & 1) * 2; }
-    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+    __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t) {
         const uint32_t Cp = cpad(A);
         row4 = Cp * 16;
         const uint32_t base_c = smem_addr(smem);
@@ -352,7 +353,7 @@ struct LutPair {
     }
     __device__ __forceinline__ uint32_t enc(uint32_t id) const { return (id >> 1) * NP * 128 + (id & 1) * 2; }
     __device__ __forceinline__ uint32_t id(uint32_t e) const { return ((e >> 7) / NP) * 2 + ((e >> 1) & 1); }
-    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+    __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t) {
         C = A.C;
         NP = C * C + C;
         const uint32_t base_c = smem_addr(smem);
@@ -405,7 +406,7 @@ struct LutPairC {
         return 256 * 128 + static_cast<size_t>(A.n + 1) * np_of(A) * 2;
     }
     static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n + 1) * np_of(A) * 2 <= 0xFFFF; }
-    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+    __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t) {
         C = A.C;
         const uint32_t NP = C * C + C;
         row = 2 * NP;
@@ -440,6 +441,65 @@ struct LutPairC {
     }
 };
 
+// Two-byte transitions in F lane copies (F = 2, 4, 8 or 16, chosen at launch and passed to setup),
+// for automata whose fully replicated pair table (LutPair, F = 32) does not fit: lane l reads copy
+// l & (F - 1), entry (s, p) at byte (((s >> 1) * NP + p) * F + (l & (F - 1))) * 4 + (s & 1) * 2,
+// i.e. LutPair's layout with F copies of each word side by side.  Lanes of different copies never
+// share a bank, so a pair gather costs at most 32/F wavefronts (2 at F = 16; about 3 on average at
+// F = 8 for random rows).  Against the half-replicated single-byte table (LutPart: 2 wavefronts
+// a lookup) a pair gather pays for two bytes.  Entries enc(s) = (s >> 1) * NP * 4F + (s & 1) * 2;
+// class words c * 4F, so a pair step is s' = T[s + cw1 * C + cw2] and a single step
+// s' = T[s + C*C*4F + cw], as in LutPair.  Needs (P/2 + 1) * NP * 4F <= 64 KiB.
+struct LutPairF {
+    static constexpr bool kPairs = true;
+    uint32_t lc, lt, lt1;     // this lane's class copy; its transition copy (pairs, singles)
+    uint32_t C, NP, F4;       // F4 = 4F: bytes per word row
+    static uint32_t np_of(const Automaton &A) { return A.C * A.C + A.C; }
+    static size_t smem_bytes(const Automaton &A, uint32_t F) {
+        return 256 * 128 + static_cast<size_t>((A.n + 2) / 2) * np_of(A) * 4 * F;
+    }
+    static bool fits(const Automaton &A, uint32_t F) {
+        return (static_cast<uint64_t>(A.n / 2) + 1) * np_of(A) * 4 * F <= 0xFFFF;
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return (id >> 1) * NP * F4 + (id & 1) * 2; }
+    __device__ __forceinline__ uint32_t id(uint32_t e) const { return ((e / F4) / NP) * 2 + ((e >> 1) & 1); }
+    // aux = F, the number of lane copies
+    __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t aux) {
+        const uint32_t F = aux;
+        C = A.C;
+        NP = C * C + C;
+        F4 = 4 * F;
+        const uint32_t base_c = smem_addr(smem);
+        const uint32_t base_t = base_c + 256 * 128;
+        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) sts_u32(base_c + i * 4, A.classmap[i >> 5] * F4);
+        const uint32_t n = A.n;               // the dead state: row n maps to itself
+        auto step = [&](uint32_t st, uint32_t c) { return st >= n ? n : static_cast<uint32_t>(A.trans[st * C + c]); };
+        auto value = [&](uint32_t st, uint32_t col) {
+            if (st > n) st = n;
+            const uint32_t t = col < C * C ? step(step(st, col / C), col % C) : step(st, col - C * C);
+            return enc(t);
+        };
+        const uint32_t words = ((n + 2) / 2) * NP;
+        for (uint32_t i = threadIdx.x; i < words * F; i += blockDim.x) {
+            const uint32_t w = i / F;
+            const uint32_t sp = w / NP, col = w % NP;
+            sts_u32(base_t + i * 4, value(2 * sp, col) | (value(2 * sp + 1, col) << 16));
+        }
+        const uint32_t lane = threadIdx.x & 31;
+        lc = base_c + lane * 4;
+        lt = base_t + (lane & (F - 1)) * 4;
+        lt1 = lt + C * C * F4;
+    }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return lds_u16(lt1 + s + c); }
+    __device__ __forceinline__ uint32_t pair_col(uint32_t c1, uint32_t c2) const { return c1 * C + c2; }
+    __device__ __forceinline__ uint32_t next_pc(uint32_t s, uint32_t pc) const { return lds_u16(lt + s + pc); }
+    __device__ __forceinline__ uint32_t next2(uint32_t s, uint32_t c1, uint32_t c2) const {
+        return next_pc(s, pair_col(c1, c2));
+    }
+};
+
 template <class LUT, class = void>
 struct has_pairs { static constexpr bool value = false; };
 template <class LUT>
@@ -461,7 +521,7 @@ struct LutPart {
     }
     static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n) * cpad(A) * F <= 0xFFFF; }
     __device__ __forceinline__ static uint32_t cls_off(uint32_t c) { return (c >> 1) * (4 * F) + (c & 1) * 2; }
-    __device__ void setup(const Automaton &A, uint8_t *smem, bool) {
+    __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t) {
         const uint32_t Cp = cpad(A);
         unit = Cp * F;
         const uint32_t base_c = smem_addr(smem);

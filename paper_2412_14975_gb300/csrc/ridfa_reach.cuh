@@ -11,13 +11,15 @@ namespace ridfa {
 
 // table layouts (ridfa_tuning::table_mode)
 enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3, kModePart16 = 4, kModeFlat = 5,
-                       kModeRep16x4 = 6, kModeRep16x4C = 7, kModePair = 8, kModePairC = 9 };
+                       kModeRep16x4 = 6, kModeRep16x4C = 7, kModePair = 8, kModePairC = 9,
+                       kModePairF = 10 };
 
 // How one reach launch is laid out: table layout, text path, block/grid, shared memory.
 struct ReachPlan {
     uint32_t mode = kModePlain;
     int R = 1;
-    int tis = 0;                 // compact table in shared memory (Plain only)
+    int tis = 0;                 // layout parameter: Flat, table in shared memory (1) or not (0);
+                                 // PairF, the number of lane copies
     int path = kPathGlobal;      // how the converged phase reads the text
     int block = 256;
     int grid = 1;
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach_kernel(ReachArgs p, int ta
     extern __shared__ __align__(128) uint8_t smem[];
     const Automaton &A = p.A;
     LUT T;
-    T.setup(A, smem, table_in_smem != 0);
+    T.setup(A, smem, static_cast<uint32_t>(table_in_smem));
     // per-warp staging buffers of the cooperative text paths
     const uint32_t warp_in_block = threadIdx.x >> 5;
     const uint32_t stg_base = smem_addr(smem) + staging_offset + warp_in_block * kWarpCoopBytes;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rid_reach2_kernel(ReachArgs p, int t
     extern __shared__ __align__(128) uint8_t smem[];
     const Automaton &A = p.A;
     LUT T;
-    T.setup(A, smem, table_in_smem != 0);
+    T.setup(A, smem, static_cast<uint32_t>(table_in_smem));
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t stg = smem_addr(smem) + staging_offset + (threadIdx.x >> 5) * kWarpCoop2Bytes;
@@ -463,6 +465,9 @@ cudaError_t reach_m(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, in
         case kModePair:
             // (two-byte steps serve the single-run cooperative path and plain global loads)
             if constexpr (PATH == kPathCoop || PATH == kPathGlobal) return reach_r<LutPair, PATH>(a, pl, st, per_sm);
+            else return cudaErrorInvalidValue;
+        case kModePairF:
+            if constexpr (PATH == kPathCoop || PATH == kPathGlobal) return reach_r<LutPairF, PATH>(a, pl, st, per_sm);
             else return cudaErrorInvalidValue;
         case kModePairC:
             // (the compact two-byte table serves the set path and plain global loads)
