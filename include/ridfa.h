@@ -113,10 +113,14 @@ typedef struct {
                                  offsets (pair and single columns), a lane's runs sharing each
                                  pair's column ((P + 1) * (C*C + C) <= 32767; text paths 1 and 5
                                  only); 10 two-byte steps in F lane copies (the layout of 8 with
-                                 16, 8, 4 or 2 copies, the most whose 16-bit entries fit, at most
-                                 32/F wavefronts a lookup: (P/2 + 1) * (C*C + C) * 4F <= 65535;
-                                 text paths 1 and 3 only) (E_ARG if the chosen layout does not
-                                 fit) */
+                                 16, 8, 4 or 2 copies side by side and rows of an odd number of
+                                 words, at most 32/F wavefronts a lookup; F the most copies whose
+                                 16-bit byte offsets fit and that leave shared memory for the
+                                 launch's warps: (P/2 + 1) * ((C*C + C) | 1) * 4F <= 65535); 11 as
+                                 10 with half-word offsets (twice the copies in 16 bits) and one
+                                 256-byte table of 8-bit class offsets ((P/2 + 1) * ((C*C + C) | 1)
+                                 * 2F <= 65535, (C - 1) * 2F <= 255); 10 and 11: text paths 1 and
+                                 3 only (E_ARG if the chosen layout does not fit) */
     uint32_t text_path;       /* how the converged runs read the text: 0 auto; 1 each lane's own
                                  16-byte global loads; 2 retired (per-lane bulk copies; E_ARG);
                                  3 warp-cooperative coalesced loads staged in shared memory; 4

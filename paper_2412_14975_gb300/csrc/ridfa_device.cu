@@ -817,6 +817,7 @@ cudaError_t piece_dispatch(const ReachArgs &a, const ReachPlan &pl, int sms, cud
         case kModePair: return piece_r<LutPair>(pl.R, a, grid, smem, pl.tis, st);
         case kModePairC: return piece_r<LutPairC>(pl.R, a, grid, smem, pl.tis, st);
         case kModePairF: return piece_r<LutPairF>(pl.R, a, grid, smem, pl.tis, st);
+        case kModePairH: return piece_r<LutPairH>(pl.R, a, grid, smem, pl.tis, st);
         case kModePlain: return piece_r<LutPlain>(pl.R, a, grid, smem, pl.tis, st);
         default: return piece_r<LutFlat>(pl.R, a, grid, smem, pl.tis, st);
     }
@@ -870,13 +871,32 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
                ok16x4c = LutRep16x4C::fits(A) && rep16x4c + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit,
                okpair = LutPair::fits(A) && pair + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit,
                okpairc = LutPairC::fits(A) && pairc + 4 * static_cast<size_t>(kWarpCoopBytes) <= limit;
-    // the most lane copies (16, 8, 4 or 2) of the two-byte table whose entries fit 16 bits and that
-    // leave room for 16 warps' staging (0: none)
-    uint32_t pair_f = 0;
-    for (uint32_t f = 16; f >= 2 && !pair_f; f /= 2)
-        if (LutPairF::fits(A, f) && LutPairF::smem_bytes(A, f) + 16 * static_cast<size_t>(kWarpCoopBytes) <= limit)
-            pair_f = f;
+    // two-byte tables in lane copies (byte and half-word offsets): the most copies (16, 8, 4 or 2)
+    // whose entries fit 16 bits and that leave room beside the table for the warps the launch
+    // wants, one per task up to the block cap (a table that leaves fewer starts a second round of
+    // tasks: the any-field record lines with half-word offsets at 4 copies, 28 warps for 32 tasks
+    // per SM, ran at 1,647 against 2,782 GB/s at 2 copies); on request, room for 4 warps is enough
+    const uint64_t coop_tasks = (static_cast<uint64_t>(ra.c) + 31) / 32;
+    const size_t w_want = std::min<uint64_t>(pl.R <= 4 ? 32 : 16,
+                                             std::max<uint64_t>(4, (coop_tasks + sms - 1) / sms));
+    auto copies = [&](auto fits_f, auto bytes_f, size_t warps) -> uint32_t {
+        for (uint32_t f = 16; f >= 2; f /= 2) {
+            if (!fits_f(f)) continue;
+            const size_t t = (bytes_f(f) + 127) & ~static_cast<size_t>(127);
+            if (t + warps * kWarpCoopBytes <= limit) return f;
+        }
+        return 0;
+    };
+    auto f_fits = [&](uint32_t f) { return LutPairF::fits(A, f); };
+    auto f_bytes = [&](uint32_t f) { return LutPairF::smem_bytes(A, f); };
+    auto h_fits = [&](uint32_t f) { return LutPairH::fits(A, f); };
+    auto h_bytes = [&](uint32_t f) { return LutPairH::smem_bytes(A, f); };
+    const uint32_t want_mode = tuning ? tuning->table_mode : 0;
+    uint32_t pair_f = copies(f_fits, f_bytes, w_want), pair_h = copies(h_fits, h_bytes, w_want);
+    if (want_mode == kModePairF && !pair_f) pair_f = copies(f_fits, f_bytes, 4);
+    if (want_mode == kModePairH && !pair_h) pair_h = copies(h_fits, h_bytes, 4);
     const size_t pairf = pair_f ? LutPairF::smem_bytes(A, pair_f) : 0;
+    const size_t pairh = pair_h ? LutPairH::smem_bytes(A, pair_h) : 0;
     // replicated layouts that leave room for at least 16 warps' staging come first; a 32-bit table
     // that leaves fewer is taken only when no scaled 16-bit one fits (measured: a 6-warp 32-bit
     // table ran at a third of the speed of a 26-warp scaled one)
@@ -914,28 +934,35 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
         if (allow_pair && mode == kModePlain && okplain && okpairc && (tp == 0 || tp == 1 || tp == 5) &&
             pairc + 16 * static_cast<size_t>(kWarpCoopBytes) <= limit)
             mode = kModePairC;
-        // the half-replicated one-byte table gives way to the two-byte table in as many lane
-        // copies as fit (a pair gather of at most 32/F wavefronts pays for two bytes where a
-        // half-replicated lookup costs up to 2 for one): regexp family k = 7 (8 copies) 2,200 ->
-        // 2,284 GB/s, the any-field record lines (2 copies) 2,559 -> 2,777; not where the fully
-        // replicated pair table fits (regexp k = 5: 16 copies ran 10 % slower than 32)
-        if (allow_pair && mode == kModePart16 && pair_f && (tp == 0 || tp == 1 || tp == 3))
-            mode = kModePairF;
+        // the half-replicated one-byte table gives way to the two-byte table in lane copies (a pair
+        // gather of at most 32/F wavefronts pays for two bytes where a half-replicated lookup costs
+        // up to 2 for one): byte offsets at 16 copies, else half-word offsets at 16 copies (one
+        // shift-add more a step; regexp family k = 7: 2,658 GB/s against 2,413 with byte offsets
+        // at 8 copies and 2,289 with Part16), else byte offsets at the most copies that fit (the
+        // any-field record lines, 2 copies: 2,876 against 2,782); not where the fully replicated
+        // pair table fits (regexp k = 5: 16 copies ran 10 % slower than 32)
+        if (allow_pair && mode == kModePart16 && (tp == 0 || tp == 1 || tp == 3)) {
+            if (pair_f == 16 || (pair_f && pair_h != 16)) mode = kModePairF;
+            else if (pair_h == 16) mode = kModePairH;
+        }
     }
     if (mode == kModeRep16x4 && !ok16x4) return RIDFA_E_ARG;
     if (mode == kModeRep16x4C && !ok16x4c) return RIDFA_E_ARG;
     if (mode == kModePair && !okpair) return RIDFA_E_ARG;
     if (mode == kModePairC && !okpairc) return RIDFA_E_ARG;
     if (mode == kModePairF && !pair_f) return RIDFA_E_ARG;
+    if (mode == kModePairH && !pair_h) return RIDFA_E_ARG;
     if (mode == kModePlain && !okplain) mode = kModeFlat;    // the compact table, through generic loads
     if ((mode == kModeRep16 && !ok16) || (mode == kModeRep32 && !ok32) || (mode == kModePart16 && !okp))
         return RIDFA_E_ARG;
-    if (mode < kModePlain || mode > kModePairF) return RIDFA_E_ARG;
+    if (mode < kModePlain || mode > kModePairH) return RIDFA_E_ARG;
     pl.mode = mode;
-    pl.tis = mode == kModePairF ? static_cast<int>(pair_f) : (mode == kModeFlat && flat <= limit) ? 1 : 0;
+    pl.tis = mode == kModePairF ? static_cast<int>(pair_f) : mode == kModePairH ? static_cast<int>(pair_h)
+             : (mode == kModeFlat && flat <= limit) ? 1 : 0;
     const size_t table_smem = mode == kModeRep16 ? rep16 : mode == kModeRep32 ? rep32 : mode == kModePart16 ? part16
                               : mode == kModeRep16x4 ? rep16x4 : mode == kModeRep16x4C ? rep16x4c
                               : mode == kModePair ? pair : mode == kModePairC ? pairc : mode == kModePairF ? pairf
+                              : mode == kModePairH ? pairh
                               : mode == kModePlain ? plain : (pl.tis ? flat : 256);
     const int cap = pl.R <= 4 ? 1024 : 512;
     const uint32_t text_path = tuning ? tuning->text_path : 0;
@@ -979,7 +1006,7 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     if (mode == kModeRep16x4C && pl.path != kPathCoopSet && pl.path != kPathGlobal) return RIDFA_E_ARG;
     if (mode == kModePair && pl.path != kPathCoop && pl.path != kPathGlobal) return RIDFA_E_ARG;
     if (mode == kModePairC && pl.path != kPathCoopSet && pl.path != kPathGlobal) return RIDFA_E_ARG;
-    if (mode == kModePairF && pl.path != kPathCoop && pl.path != kPathGlobal) return RIDFA_E_ARG;
+    if ((mode == kModePairF || mode == kModePairH) && pl.path != kPathCoop && pl.path != kPathGlobal) return RIDFA_E_ARG;
     const int warps_fit = pl.path == kPathCoop      ? w_coop
                           : pl.path == kPathCoopSet ? w_set
                           : pl.path == kPathCoop2 ? w_coop2

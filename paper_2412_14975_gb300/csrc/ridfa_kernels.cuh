@@ -391,24 +391,29 @@ struct LutPair {
 // Two-byte transitions in one compact table, for automata whose runs stay apart (the set path,
 // where a lane steps all of its chunk's runs over the same bytes): row s holds NP = C*C + C 16-bit
 // entries, the C*C pair columns (c1, c2) -> delta(delta(s, c1), c2) and then the C single columns,
-// each entry the premultiplied row offset 2*NP*s' of its target, so
+// padded to NPr entries (NPr = 2 mod 4: an odd number of words, so that consecutive rows start in
+// different banks and the rows of one column cover all 32), each entry the premultiplied row offset
+// 2*NPr*s' of its target, so
 //   pair step   s' = T[s + 2*(c1*C + c2)]   (the column shared by all of a lane's runs),
 //   single step s' = T[s + 2*C*C + 2*c].
 // The class table is lane-replicated (word b*32 + l = 2*class(b), conflict-free).  A lane with m
 // runs then pays 1 class lookup per byte and m/2 transition lookups instead of m; the gathers
-// into the table can share banks, as in Plain.  Needs 2*NP*(P+1) <= 64 KiB.
+// into the table can share banks, as in Plain.  Needs 2*NPr*(P+1) <= 64 KiB.
 struct LutPairC {
     static constexpr bool kPairs = true;
     uint32_t lc, bt, bt1;     // this lane's class copy; the table (pairs, singles)
-    uint32_t C, row;          // row: 2*NP bytes per state
-    static uint32_t np_of(const Automaton &A) { return A.C * A.C + A.C; }
+    uint32_t C, row;          // row: 2*NPr bytes per state
+    __host__ __device__ static uint32_t np_of(const Automaton &A) {
+        const uint32_t np = A.C * A.C + A.C;
+        return np + (6 - np % 4) % 4;          // NPr: the next count = 2 mod 4
+    }
     static size_t smem_bytes(const Automaton &A) {
         return 256 * 128 + static_cast<size_t>(A.n + 1) * np_of(A) * 2;
     }
     static bool fits(const Automaton &A) { return static_cast<uint64_t>(A.n + 1) * np_of(A) * 2 <= 0xFFFF; }
     __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t) {
         C = A.C;
-        const uint32_t NP = C * C + C;
+        const uint32_t NP = np_of(A);
         row = 2 * NP;
         const uint32_t base_c = smem_addr(smem);
         bt = base_c + 256 * 128;
@@ -417,6 +422,7 @@ struct LutPairC {
         const uint32_t n = A.n;               // the dead state: row n maps to itself
         auto value = [&](uint32_t e) -> uint32_t {
             const uint32_t st = e / NP, col = e % NP;
+            if (col >= C * C + C) return 0u;  // padding, never read
             const uint32_t t = col < C * C ? A.trans[A.trans[st * C + col / C] * C + col % C]
                                            : A.trans[st * C + col - C * C];
             return t * row;
@@ -443,62 +449,100 @@ struct LutPairC {
 
 // Two-byte transitions in F lane copies (F = 2, 4, 8 or 16, chosen at launch and passed to setup),
 // for automata whose fully replicated pair table (LutPair, F = 32) does not fit: lane l reads copy
-// l & (F - 1), entry (s, p) at byte (((s >> 1) * NP + p) * F + (l & (F - 1))) * 4 + (s & 1) * 2,
-// i.e. LutPair's layout with F copies of each word side by side.  Lanes of different copies never
-// share a bank, so a pair gather costs at most 32/F wavefronts (2 at F = 16; about 3 on average at
-// F = 8 for random rows).  Against the half-replicated single-byte table (LutPart: 2 wavefronts
-// a lookup) a pair gather pays for two bytes.  Entries enc(s) = (s >> 1) * NP * 4F + (s & 1) * 2;
-// class words c * 4F, so a pair step is s' = T[s + cw1 * C + cw2] and a single step
-// s' = T[s + C*C*4F + cw], as in LutPair.  Needs (P/2 + 1) * NP * 4F <= 64 KiB.
-struct LutPairF {
+// l & (F - 1), and word (s >> 1, p) of LutPair's layout (two states per word, 16-bit halves) is
+// stored F times side by side:
+//   entry (s, p) at byte (((s >> 1) * NPw + p) * F + (l & (F - 1))) * 4 + (s & 1) * 2,
+// NPw = (C*C + C) | 1 columns per state pair (odd, so that the rows of one column fall in every
+// bank and not in one: with an even row stride all lanes of a copy reading one column would meet
+// in the same bank or two).  Lanes of different copies never share a bank, so a pair gather costs
+// at most 32/F wavefronts (2 at F = 16; about 3 on average at F = 8 for random rows), and it pays
+// for two bytes, where the half-replicated one-byte table (LutPart) costs up to 2 for one.
+// Two forms:
+//   HW = false: entries are byte offsets enc(s) = (s >> 1) * NPw * 4F + (s & 1) * 2 beside the
+//     lane-replicated class table (word b*32 + l = class(b) * 4F): a pair step is one IMAD for the
+//     column and s' = T[s + cw1*C + cw2], one add and one load.  Needs (P/2 + 1) * NPw * 4F <= 64 KiB.
+//   HW = true: entries are half-word offsets enc(s) = (s >> 1) * NPw * 2F + (s & 1), so twice the
+//     copies fit 16 bits, beside one 256-byte table of 8-bit class offsets class(b) * 2F (bytes
+//     below 128 read distinct banks, so ASCII text never conflicts there); a step is
+//     s' = T[2 * (s + column)], one shift-add more.  Needs (P/2 + 1) * NPw * 2F <= 64 Ki and
+//     (C - 1) * 2F <= 255.
+template <bool HW>
+struct LutPairFT {
     static constexpr bool kPairs = true;
-    uint32_t lc, lt, lt1;     // this lane's class copy; its transition copy (pairs, singles)
-    uint32_t C, NP, F4;       // F4 = 4F: bytes per word row
-    static uint32_t np_of(const Automaton &A) { return A.C * A.C + A.C; }
+    uint32_t lc, lt, lt1;     // this lane's class table; its transition copy (pairs, singles)
+    uint32_t C, NPw, FU;      // FU: offset units per word row (4F bytes, or 2F half-words)
+    __host__ __device__ static uint32_t npw_of(uint32_t C) { return (C * C + C) | 1u; }
+    __host__ __device__ static constexpr size_t class_bytes() { return HW ? 256 : 256 * 128; }
     static size_t smem_bytes(const Automaton &A, uint32_t F) {
-        return 256 * 128 + static_cast<size_t>((A.n + 2) / 2) * np_of(A) * 4 * F;
+        return class_bytes() + static_cast<size_t>((A.n + 2) / 2) * npw_of(A.C) * 4 * F;
     }
     static bool fits(const Automaton &A, uint32_t F) {
-        return (static_cast<uint64_t>(A.n / 2) + 1) * np_of(A) * 4 * F <= 0xFFFF;
+        const uint64_t fu = HW ? 2 * F : 4 * F;
+        return (static_cast<uint64_t>(A.n / 2) + 1) * npw_of(A.C) * fu <= 0xFFFF &&
+               (!HW || (A.C - 1) * fu <= 255);
     }
-    __device__ __forceinline__ uint32_t enc(uint32_t id) const { return (id >> 1) * NP * F4 + (id & 1) * 2; }
-    __device__ __forceinline__ uint32_t id(uint32_t e) const { return ((e / F4) / NP) * 2 + ((e >> 1) & 1); }
+    __device__ __forceinline__ uint32_t enc(uint32_t id) const {
+        return (id >> 1) * NPw * FU + (id & 1) * (HW ? 1 : 2);
+    }
+    __device__ __forceinline__ uint32_t id(uint32_t e) const {
+        return ((e / FU) / NPw) * 2 + (HW ? (e & 1) : ((e >> 1) & 1));
+    }
     // aux = F, the number of lane copies
     __device__ void setup(const Automaton &A, uint8_t *smem, uint32_t aux) {
         const uint32_t F = aux;
         C = A.C;
-        NP = C * C + C;
-        F4 = 4 * F;
+        const uint32_t NP = C * C + C;
+        NPw = npw_of(C);
+        FU = HW ? 2 * F : 4 * F;
         const uint32_t base_c = smem_addr(smem);
-        const uint32_t base_t = base_c + 256 * 128;
-        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) sts_u32(base_c + i * 4, A.classmap[i >> 5] * F4);
+        const uint32_t base_t = base_c + static_cast<uint32_t>(class_bytes());
+        if (HW) {
+            for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) {
+                uint32_t v = 0;
+                for (uint32_t q = 0; q < 4; ++q) v |= (A.classmap[4 * i + q] * FU) << (8 * q);
+                sts_u32(base_c + i * 4, v);
+            }
+        } else {
+            for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) sts_u32(base_c + i * 4, A.classmap[i >> 5] * FU);
+        }
         const uint32_t n = A.n;               // the dead state: row n maps to itself
         auto step = [&](uint32_t st, uint32_t c) { return st >= n ? n : static_cast<uint32_t>(A.trans[st * C + c]); };
         auto value = [&](uint32_t st, uint32_t col) {
             if (st > n) st = n;
+            if (col >= NP) return 0u;         // padding column, never read
             const uint32_t t = col < C * C ? step(step(st, col / C), col % C) : step(st, col - C * C);
             return enc(t);
         };
-        const uint32_t words = ((n + 2) / 2) * NP;
+        const uint32_t words = ((n + 2) / 2) * NPw;
         for (uint32_t i = threadIdx.x; i < words * F; i += blockDim.x) {
             const uint32_t w = i / F;
-            const uint32_t sp = w / NP, col = w % NP;
+            const uint32_t sp = w / NPw, col = w % NPw;
             sts_u32(base_t + i * 4, value(2 * sp, col) | (value(2 * sp + 1, col) << 16));
         }
         const uint32_t lane = threadIdx.x & 31;
-        lc = base_c + lane * 4;
+        lc = HW ? base_c : base_c + lane * 4;
         lt = base_t + (lane & (F - 1)) * 4;
-        lt1 = lt + C * C * F4;
+        lt1 = lt + C * C * FU * (HW ? 2 : 1);
     }
-    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const { return lds_u32(lc + b * 128); }
-    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const { return lds_u32(lc + (byte_of(w, q) << 7)); }
-    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const { return lds_u16(lt1 + s + c); }
+    __device__ __forceinline__ uint32_t cls_of(uint32_t b) const {
+        return HW ? lds_u8(lc + b) : lds_u32(lc + b * 128);
+    }
+    __device__ __forceinline__ uint32_t cls_at(uint32_t w, int q) const {
+        return HW ? lds_u8(lc + byte_of(w, q)) : lds_u32(lc + (byte_of(w, q) << 7));
+    }
+    __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const {
+        return HW ? lds_u16(lt1 + ((s + c) << 1)) : lds_u16(lt1 + s + c);
+    }
     __device__ __forceinline__ uint32_t pair_col(uint32_t c1, uint32_t c2) const { return c1 * C + c2; }
-    __device__ __forceinline__ uint32_t next_pc(uint32_t s, uint32_t pc) const { return lds_u16(lt + s + pc); }
+    __device__ __forceinline__ uint32_t next_pc(uint32_t s, uint32_t pc) const {
+        return HW ? lds_u16(lt + ((s + pc) << 1)) : lds_u16(lt + s + pc);
+    }
     __device__ __forceinline__ uint32_t next2(uint32_t s, uint32_t c1, uint32_t c2) const {
         return next_pc(s, pair_col(c1, c2));
     }
 };
+using LutPairF = LutPairFT<false>;
+using LutPairH = LutPairFT<true>;
 
 template <class LUT, class = void>
 struct has_pairs { static constexpr bool value = false; };

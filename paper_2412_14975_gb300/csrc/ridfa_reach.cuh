@@ -12,14 +12,14 @@ namespace ridfa {
 // table layouts (ridfa_tuning::table_mode)
 enum Mode : uint32_t { kModePlain = 1, kModeRep16 = 2, kModeRep32 = 3, kModePart16 = 4, kModeFlat = 5,
                        kModeRep16x4 = 6, kModeRep16x4C = 7, kModePair = 8, kModePairC = 9,
-                       kModePairF = 10 };
+                       kModePairF = 10, kModePairH = 11 };
 
 // How one reach launch is laid out: table layout, text path, block/grid, shared memory.
 struct ReachPlan {
     uint32_t mode = kModePlain;
     int R = 1;
     int tis = 0;                 // layout parameter: Flat, table in shared memory (1) or not (0);
-                                 // PairF, the number of lane copies
+                                 // PairF / PairH, the number of lane copies
     int path = kPathGlobal;      // how the converged phase reads the text
     int block = 256;
     int grid = 1;
@@ -468,6 +468,9 @@ cudaError_t reach_m(const ReachArgs &a, const ReachPlan &pl, cudaStream_t st, in
             else return cudaErrorInvalidValue;
         case kModePairF:
             if constexpr (PATH == kPathCoop || PATH == kPathGlobal) return reach_r<LutPairF, PATH>(a, pl, st, per_sm);
+            else return cudaErrorInvalidValue;
+        case kModePairH:
+            if constexpr (PATH == kPathCoop || PATH == kPathGlobal) return reach_r<LutPairH, PATH>(a, pl, st, per_sm);
             else return cudaErrorInvalidValue;
         case kModePairC:
             // (the compact two-byte table serves the set path and plain global loads)

@@ -539,12 +539,13 @@ def test_compact_two_byte_layout():
     assert e.value.code == -1
 
 
-def test_two_byte_lane_copies_layout():
-    """Table layout 10 (two-byte steps in F lane copies, F = 16, 8, 4 or 2 by size): every row
-    equals the oracle's on the regexp family k = 5 (16 copies) and k = 7 (8), the any-field record
-    lines and the codon RE (2), aligned (staged) and unaligned (global loads) texts, bytes outside
-    the alphabet, few chunks (pieces), and on the DFA comparator where it fits; automata whose
-    pair table fits no copy count, and the set path, refuse it."""
+@pytest.mark.parametrize("mode", [10, 11])
+def test_two_byte_lane_copies_layout(mode):
+    """Table layouts 10 and 11 (two-byte steps in F lane copies, F = 16, 8, 4 or 2 by size; byte
+    and half-word offsets): every row equals the oracle's on the regexp family k = 5 and k = 7,
+    the any-field record lines and the codon RE, aligned (staged) and unaligned (global loads)
+    texts, bytes outside the alphabet, few chunks (pieces), and on the DFA comparator where it
+    fits; automata whose pair table fits no copy count, and the set path, refuse it."""
     cases = ((textgen.regexp_family_re(5), textgen.regexp_family_text(200_003, seed=501), True),
              (textgen.regexp_family_re(7), textgen.regexp_family_text(300_001, seed=502), True),
              (textgen.C3_RE_ANYFIELD, textgen.c3_text(1 << 18, seed=503), True),
@@ -552,29 +553,29 @@ def test_two_byte_lane_copies_layout():
     for re_src, x, dfa in cases:
         for c in (1, 7, 1000, 4099):
             check(re_src, x, c, dfa_too=dfa, rows=list(range(c)) if c <= 1000 else None,
-                  tuning=dict(table_mode=10))
+                  tuning=dict(table_mode=mode))
         y, _ = textgen.mutate(x, seed=505, n_subs=3, alphabet=b"ACGTabN\n")
-        check(re_src, y, 1000, dfa_too=dfa, rows=list(range(1000)), tuning=dict(table_mode=10))
-        check(re_src, x, 1000, dfa_too=dfa, rows=list(range(1000)), tuning=dict(table_mode=10, text_path=1))
+        check(re_src, y, 1000, dfa_too=dfa, rows=list(range(1000)), tuning=dict(table_mode=mode))
+        check(re_src, x, 1000, dfa_too=dfa, rows=list(range(1000)), tuning=dict(table_mode=mode, text_path=1))
         prog = lib.ridfa_compile(re_src)
         o, ser = oracle(re_src)
         base = torch.from_numpy(np.concatenate([np.zeros(16, np.uint8), x])).to("cuda:0")
         z = x[9:]
         maps = torch.empty((300, prog.info["k"]), dtype=torch.int16, device="cuda:0")
-        acc = lib.ridfa_recognize(prog, base[16 + 9:], z.size, 300, tuning=dict(table_mode=10), d_chunk_maps=maps)
+        acc = lib.ridfa_recognize(prog, base[16 + 9:], z.size, 300, tuning=dict(table_mode=mode), d_chunk_maps=maps)
         assert acc == ser.accepts(z)
         got = maps.cpu().numpy().view(np.uint16)
         want = o.lambda_rows(z, 300, [0, 1, 150, 298, 299])
         for i in want:
             assert np.array_equal(got[i], want[i])
         with pytest.raises(lib.RidfaError) as e:
-            lib.ridfa_recognize(prog, to_device(x), x.size, 1000, tuning=dict(table_mode=10, text_path=5))
+            lib.ridfa_recognize(prog, to_device(x), x.size, 1000, tuning=dict(table_mode=mode, text_path=5))
         assert e.value.code == -1
     # 4,121 states x 12 columns: even 2 copies overflow the 16-bit entries
     prog = lib.ridfa_compile(textgen.regexp_family_re(11))
     x = textgen.regexp_family_text(1 << 16, seed=506)
     with pytest.raises(lib.RidfaError) as e:
-        lib.ridfa_recognize(prog, to_device(x), x.size, 100, tuning=dict(table_mode=10))
+        lib.ridfa_recognize(prog, to_device(x), x.size, 100, tuning=dict(table_mode=mode))
     assert e.value.code == -1
 
 
