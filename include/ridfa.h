@@ -348,6 +348,19 @@ int ridfa_last_status(const ridfa_program *prog, void *stream);
  * events.  Errors: E_ARG (no profiled call yet), E_CUDA. */
 int ridfa_last_timings(const ridfa_program *prog, float *reach_ms, float *join_ms);
 
+/* The reach plan of the last ridfa_recognize / ridfa_recognize_dfa / ridfa_recognize_host call of
+ * `prog` on the current device (diagnostics; the automatic choices the tuning fields override). */
+typedef struct {
+    uint32_t table_mode;    /* table layout, numbered as ridfa_tuning::table_mode (1..11) */
+    uint32_t text_path;     /* 1 global loads, 3 staged, 4 staged two chunks a lane, 5 set path */
+    uint32_t lane_copies;   /* copies F of layouts 10 and 11, else 0 */
+    uint32_t block_threads; /* threads per block of the reach launch */
+    uint32_t grid_blocks;   /* blocks of the reach launch */
+    uint32_t pieces;        /* 1: the chunks were cut into pieces (intra-chunk speculation) */
+} ridfa_plan_report;
+/* Errors: E_ARG (prog or out NULL, or no call on this device yet), E_CUDA. */
+int ridfa_last_plan(const ridfa_program *prog, ridfa_plan_report *out);
+
 /* ---- Batched recognition (the paper recognises one text at a time; a batch runs the same
  * reach and join, exactly, for many (text, program) items at once).
  * All items' chunks run in one persistent reach launch per shared-memory table layout (CTAs take

@@ -13,7 +13,7 @@ from ._lib import (RIDFA_MAX_SLOTS, RIDFA_MAX_STATES, RIDFA_NOALLOC_SCRATCH_BYTE
                    RIDFA_UNDEF, Program, RidfaError, ridfa_recognize_noalloc,
                    ridfa_bench_hbm_read, ridfa_bench_smem_gather,
                    Tuning, lib_path, ridfa_compile, ridfa_delegates, ridfa_export_tables,
-                   ridfa_free, ridfa_last_status, ridfa_last_timings, ridfa_program_info, ridfa_recognize,
+                   ridfa_free, ridfa_last_plan, ridfa_last_status, ridfa_last_timings, ridfa_program_info, ridfa_recognize,
                    ridfa_recognize_async, ridfa_recognize_dfa, ridfa_recognize_dfa_async, ridfa_recognize_nfa, ridfa_recognize_host, ridfa_check_bounded_wait,
                    ridfa_slots, ridfa_state_set, ridfa_strerror,
                    Batch, ridfa_batch_create, ridfa_batch_run, ridfa_batch_get_stats, ridfa_batch_free,

@@ -71,6 +71,14 @@ _decl("ridfa_strerror", _c.c_char_p, [_c.c_int])
 _decl("ridfa_last_timings", _c.c_int, [_vp, _c.POINTER(_c.c_float), _c.POINTER(_c.c_float)])
 
 
+class PlanReport(_c.Structure):
+    _fields_ = [("table_mode", _u32), ("text_path", _u32), ("lane_copies", _u32),
+                ("block_threads", _u32), ("grid_blocks", _u32), ("pieces", _u32)]
+
+
+_decl("ridfa_last_plan", _c.c_int, [_vp, _c.POINTER(PlanReport)])
+
+
 class RidfaError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -280,6 +288,14 @@ def ridfa_recognize_nfa(prog, d_text, length, n_chunks, d_sets=None, stream=None
 def ridfa_last_status(prog, stream=None):
     code = _lib.ridfa_last_status(prog, _stream(stream))
     return code
+
+
+def ridfa_last_plan(prog):
+    """The reach plan of the program's last recognition on the current device: dict with
+    table_mode, text_path, lane_copies, block_threads, grid_blocks, pieces."""
+    out = PlanReport()
+    _check(_lib.ridfa_last_plan(prog, _c.byref(out)), "ridfa_last_plan")
+    return {f: getattr(out, f) for f, _ in out._fields_}
 
 
 def ridfa_last_timings(prog):

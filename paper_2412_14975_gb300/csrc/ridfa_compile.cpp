@@ -507,6 +507,53 @@ void set_final_bits(ridfa::HostAutomaton &A) {
         if (A.final_flag[p]) A.final_bits[p >> 5] |= 1u << (p & 31);
 }
 
+// A planning hint, not part of the method: whether the runs from every slot merge into about one
+// on text that follows no structure.  For 16 seeded random class sequences over the live classes
+// (those with a defined move from some state), the distinct live states 64 bytes after starting
+// in every slot state are counted (0 when all died); merges = 1 when they average at most 1.25.
+// Automata whose runs merge are served best by one run per lane after the hand-off; those whose
+// runs stay apart (the codon RE's reading frames) by a lane carrying all of its chunk's runs.
+void merge_hint(ridfa::HostAutomaton &A) {
+    const uint32_t n = A.n_states, C = A.n_classes;
+    std::vector<uint32_t> live;
+    for (uint32_t c = 0; c < C; ++c)
+        for (uint32_t s = 0; s < n; ++s)
+            if (A.trans[static_cast<size_t>(s) * C + c] != n) {
+                live.push_back(c);
+                break;
+            }
+    A.merges = 1;
+    if (live.empty() || A.k == 0) return;
+    uint64_t x = 0x9E3779B97F4A7C15ull;        // splitmix64 state, fixed seed
+    auto next = [&]() {
+        uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    std::vector<uint32_t> st, st2, seen(n + 1, 0);
+    uint32_t gen = 0, total = 0;
+    const uint32_t trials = 16;
+    for (uint32_t t = 0; t < trials; ++t) {
+        st.assign(A.slot_state.begin(), A.slot_state.end());
+        for (uint32_t i = 0; i < 64 && !st.empty(); ++i) {
+            const uint32_t c = live[next() % live.size()];
+            ++gen;
+            st2.clear();
+            for (uint32_t s : st) {
+                const uint32_t s2 = A.trans[static_cast<size_t>(s) * C + c];
+                if (s2 != n && seen[s2] != gen) {
+                    seen[s2] = gen;
+                    st2.push_back(s2);
+                }
+            }
+            st.swap(st2);
+        }
+        total += static_cast<uint32_t>(st.size());
+    }
+    A.merges = 4 * total <= 5 * trials ? 1u : 0u;
+}
+
 // RI-DFA and its interface (Sec. 3.1, 3.2, 3.4).
 void build_rid(const ClassNfa &N, uint32_t cap, bool minimize, ridfa_program &P) {
     SubsetMachine M;
@@ -597,6 +644,7 @@ void build_rid(const ClassNfa &N, uint32_t cap, bool minimize, ridfa_program &P)
             uint32_t a = P.delegate_slot[q];
             A.ifmask[static_cast<size_t>(p) * A.kw + (a >> 5)] |= 1u << (a & 31);
         }
+    merge_hint(A);
 }
 
 // Minimal DFA for the all-states comparator (Sec. 2): powerset from {q0}, state partition,
@@ -698,6 +746,7 @@ bool build_min_dfa(const ClassNfa &N, uint32_t cap, ridfa_program &P) {
         A.slot_state[i] = static_cast<uint16_t>(i);
         A.ifmask[static_cast<size_t>(i) * A.kw + (i >> 5)] |= 1u << (i & 31);
     }
+    merge_hint(A);
     return true;
 }
 

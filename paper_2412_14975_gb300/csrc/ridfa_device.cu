@@ -931,8 +931,14 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
         // runs then share each pair's column and pay half the transition lookups (the codon RE
         // on 1 GiB, 65,536 chunks: 1,057 -> 1,256 GB/s; on the regexp family, whose replicated
         // tables keep one run a lane, the two-byte compact table measured 16 % slower)
-        if (allow_pair && mode == kModePlain && okplain && okpairc && (tp == 0 || tp == 1 || tp == 5) &&
-            pairc + 16 * static_cast<size_t>(kWarpCoopBytes) <= limit)
+        // (automata whose runs merge on random text -- the compile-time hint -- take the two-byte
+        // table in lane copies below instead, one run per lane: the regexp family k = 9, 2,067
+        // against 1,839 GB/s)
+        const bool copies_ok = pair_f || pair_h;
+        if (allow_pair && mode == kModePlain && A.merges && copies_ok && (tp == 0 || tp == 1 || tp == 3))
+            mode = kModePart16;               // (replaced by a table in lane copies just below)
+        else if (allow_pair && mode == kModePlain && okplain && okpairc && (tp == 0 || tp == 1 || tp == 5) &&
+                 pairc + 16 * static_cast<size_t>(kWarpCoopBytes) <= limit)
             mode = kModePairC;
         // the half-replicated one-byte table gives way to the two-byte table in lane copies (a pair
         // gather of at most 32/F wavefronts pays for two bytes where a half-replicated lookup costs
@@ -942,8 +948,8 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
         // any-field record lines, 2 copies: 2,876 against 2,782); not where the fully replicated
         // pair table fits (regexp k = 5: 16 copies ran 10 % slower than 32)
         if (allow_pair && mode == kModePart16 && (tp == 0 || tp == 1 || tp == 3)) {
-            if (pair_f == 16 || (pair_f && pair_h != 16)) mode = kModePairF;
-            else if (pair_h == 16) mode = kModePairH;
+            if (pair_f == 16 || (pair_f && pair_f >= pair_h)) mode = kModePairF;
+            else if (pair_h) mode = kModePairH;
         }
     }
     if (mode == kModeRep16x4 && !ok16x4) return RIDFA_E_ARG;
@@ -1088,7 +1094,7 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
         1, (nbound + static_cast<uint64_t>(kJoinThreads) * per_thread - 1) /
                (static_cast<uint64_t>(kJoinThreads) * per_thread)));
     Automaton A{D->trans, D->classmap, D->final_bits, D->ifmask, D->slot_state,
-                H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+                H.n_states, H.n_classes, H.k, H.kw, H.q0_slot, H.merges};
     // intra-chunk speculation: too few chunks to fill the GPU, each long enough to cut into pieces.
     // Pieces run from every state; automata of more than 256 states run theirs in groups of at
     // most 256 states (one reach launch per group into one row of all states).
@@ -1159,6 +1165,15 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
                                 spc > 1 ? NS : 0, comp_funcs, lookback);
     DeviceScratch *S = scratch_for(P, dev, L.total, &err);
     if (!S) return err;
+    {
+        const ReachPlan &p0 = plans[0];
+        const bool copies = p0.mode == kModePairF || p0.mode == kModePairH;
+        S->last_plan = ridfa_plan_report{p0.mode,
+                                         p0.path == kPathCoop ? 3u : p0.path == kPathCoop2 ? 4u : p0.path == kPathCoopSet ? 5u : 1u,
+                                         copies ? static_cast<uint32_t>(p0.tis) : 0u, static_cast<uint32_t>(p0.block),
+                                         static_cast<uint32_t>(p0.grid), (spc > 1 || lockstep) ? 1u : 0u};
+        S->planned = true;
+    }
     uint8_t *base = static_cast<uint8_t *>(S->base);
     uint32_t *ticket = reinterpret_cast<uint32_t *>(base + L.ticket_off);
     uint32_t *status = reinterpret_cast<uint32_t *>(base + L.status_off);
@@ -1316,7 +1331,7 @@ int launch_with_buffers(const HostAutomaton &H, const PreparedBuffers &B, const 
     const uint32_t join_blocks = static_cast<uint32_t>(std::max<uint64_t>(
         1, (nbound + kJoinThreads * per_thread - 1) / (kJoinThreads * per_thread)));
     Automaton A{B.trans, B.classmap, B.final_bits, B.ifmask, B.slot_state,
-                H.n_states, H.n_classes, H.k, H.kw, H.q0_slot};
+                H.n_states, H.n_classes, H.k, H.kw, H.q0_slot, H.merges};
     ReachArgs ra{A, d_text, len, n_chunks, B.maps, B.dinfo, B.status, 8, nullptr, nullptr, H.k};
     ReachPlan plan;
     int err = plan_reach(A, nullptr, d_text, ra, sms, &plan);
@@ -1437,6 +1452,19 @@ extern "C" int ridfa_last_status(const ridfa_program *prog, void *stream) {
         return (*s.h_status_pinned & 2u) ? RIDFA_E_STATE : RIDFA_OK;
     }
     return RIDFA_OK;
+}
+
+extern "C" int ridfa_last_plan(const ridfa_program *prog, ridfa_plan_report *out) {
+    if (!prog || !out) return RIDFA_E_ARG;
+    std::lock_guard<std::mutex> lock(prog->mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ridfa::cuda_fail(cudaGetLastError());
+    for (auto &s : prog->scratch)
+        if (s.device == dev && s.planned) {
+            *out = s.last_plan;
+            return RIDFA_OK;
+        }
+    return RIDFA_E_ARG;
 }
 
 extern "C" int ridfa_last_timings(const ridfa_program *prog, float *reach_ms, float *join_ms) {

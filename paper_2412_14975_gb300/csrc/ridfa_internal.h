@@ -37,6 +37,7 @@ struct HostAutomaton {
     std::vector<uint32_t> final_bits; // [ceil((n_states + 1) / 32)]
     std::vector<uint32_t> ifmask;     // [(n_states + 1) * kw]: slots of if_min({p}); dead row = 0
     std::vector<uint16_t> slot_state; // [k]: start state of each slot
+    uint32_t merges = 0;              // 1: runs from every slot merge on random text (merge_hint)
 };
 
 // Device copy of one automaton (one per device it was uploaded to).
@@ -84,6 +85,8 @@ struct DeviceScratch {
     uint32_t *h_status_pinned = nullptr;
     void *ev[3] = {nullptr, nullptr, nullptr};   // cudaEvent_t: before reach, before join, after
     bool profiled = false;
+    ridfa_plan_report last_plan{};               // the reach plan of the last call on this device
+    bool planned = false;
 };
 
 }  // namespace ridfa

@@ -20,6 +20,7 @@ struct Automaton {            // device view of one automaton
     const uint32_t *ifmask;   // [(n+1) * kw]
     const uint16_t *slot_state;
     uint32_t n, C, k, kw, q0_slot;
+    uint32_t merges;          // host planning hint (HostAutomaton::merges); unused on the device
 };
 
 // A run handed from the speculative phase to one lane: chunk j of the warp's task, resume

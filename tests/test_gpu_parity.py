@@ -616,3 +616,34 @@ def test_two_byte_step_layout():
     with pytest.raises(lib.RidfaError) as e:
         lib.ridfa_recognize(prog, to_device(x1), x1.size, 100, tuning=dict(table_mode=8, text_path=5))
     assert e.value.code == -1
+
+
+def test_planner_choices():
+    """The automatic plan (reported by ridfa_last_plan) takes the layouts the measurements chose:
+    lane-replicated 16-bit tables for the record lines, the compact two-byte table on the set path
+    for the codon RE (runs in three reading frames stay apart), the two-byte table in lane copies
+    with one run per lane for the regexp family (runs merge), global loads for an unaligned text;
+    an explicit layout is reported as requested.  Every answer still equals the oracle's."""
+    def plan_of(re_src, x, c, tuning=None, offset=0):
+        prog = lib.ridfa_compile(re_src)
+        _, ser = oracle(re_src)
+        base = torch.from_numpy(np.concatenate([np.zeros(16, np.uint8), x])).to("cuda:0")
+        acc = lib.ridfa_recognize(prog, base[16 + offset:], x.size - offset, c, tuning=tuning)
+        assert acc == ser.accepts(x[offset:])
+        return lib.ridfa_last_plan(prog)
+
+    p = plan_of(textgen.C3_RE, textgen.c3_text(1 << 20, seed=601), 1000)
+    assert (p["table_mode"], p["text_path"], p["lane_copies"], p["pieces"]) == (2, 3, 0, 0), p
+    re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
+    p = plan_of(re2, textgen.c2_text(1 << 20, seed=602), 1000)
+    assert (p["table_mode"], p["text_path"]) == (9, 5), p
+    p = plan_of(textgen.regexp_family_re(9), textgen.regexp_family_text(1 << 20, seed=603), 4096)
+    assert (p["table_mode"], p["text_path"]) == (11, 3) and p["lane_copies"] >= 2, p
+    p = plan_of(textgen.regexp_family_re(7), textgen.regexp_family_text(1 << 20, seed=604), 4096)
+    assert (p["table_mode"], p["text_path"], p["lane_copies"]) == (11, 3, 16), p
+    p = plan_of(textgen.C3_RE, textgen.c3_text(1 << 20, seed=605), 1000, offset=3)
+    assert p["text_path"] == 1, p
+    p = plan_of(textgen.C3_RE, textgen.c3_text(1 << 20, seed=606), 1000, tuning=dict(table_mode=1))
+    assert p["table_mode"] == 1, p
+    p = plan_of(textgen.C3_RE, textgen.c3_text(1 << 20, seed=607), 4)
+    assert p["pieces"] == 1, p
