@@ -365,7 +365,8 @@ def measure_batch(args, lib, torch, dev, stream, world, rank, steps, warmup, ora
     gen_s = time.perf_counter() - t0
     acc = torch.zeros(len(items), dtype=torch.uint8, device=dev)
     t0 = time.perf_counter()
-    b = lib.ridfa_batch_create(progs, items, acc, chunk_len=args.batch_chunk_len)
+    b = lib.ridfa_batch_create(progs, items, acc, chunk_len=args.batch_chunk_len,
+                               block_warps=args.batch_warps, set_mode=args.batch_set_mode)
     create_s = time.perf_counter() - t0
     st = lib.ridfa_batch_get_stats(b)
     for _ in range(warmup):
@@ -397,13 +398,15 @@ def measure_batch(args, lib, torch, dev, stream, world, rank, steps, warmup, ora
     def one_pass():
         for (ptr, n, r, _) in items:
             lib.ridfa_recognize_async(progs[r], ptr, n, max(1, min(n, (n + L - 1) // L)), acc1, stream=stream)
-    one_pass()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    one_pass()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    single_value = total / (e0.elapsed_time(e1) / 1e3) / 1e9
+    single_value = None
+    if not args.no_batch_single:
+        one_pass()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        one_pass()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        single_value = total / (e0.elapsed_time(e1) / 1e3) / 1e9
     # each RE's texts end to end as one long text (every RE here is star-closed, so the
     # concatenation of its members is a member), recognized alone at the best of the batch's chunk
     # length and three large chunk counts: the rate each RE reaches by itself; the batch against
@@ -452,14 +455,15 @@ def measure_batch(args, lib, torch, dev, stream, world, rank, steps, warmup, ora
                "sample": f"{len(sample)} sampled batch items ({sample_bytes} bytes), Thompson state-set simulation"}
     return {"value": round(value, 3), "unit": "GB/s", "steps": steps, "warmup": warmup,
             "ms_per_step": round(ms / steps, 4),
-            "single_text_per_launch_GBps": round(single_value, 3),
-            "batched_over_single": round(value / single_value, 3),
+            "single_text_per_launch_GBps": round(single_value, 3) if single_value else None,
+            "batched_over_single": round(value / single_value, 3) if single_value else None,
             "per_re_alone": per_re or None,
             "per_re_alone_GBps": round(total / (sep_ms / 1e3) / 1e9, 3) if sep_ms else None,
             "batched_over_per_re_alone": round(value / (total / (sep_ms / 1e3) / 1e9), 3) if sep_ms else None,
             "config": {"workload": f"batched: {len(items)} texts, lognormal median 256 KiB sigma 1, "
                                    f"16 REs (3 single-text + 13 random), half mutated, one CUDA graph",
-                       "total_bytes": total, "chunk_len": L, "chunks": st["total_chunks"],
+                       "total_bytes": total, "chunk_len": L, "block_warps": st["block_warps"],
+                       "set_mode": st["set_mode"], "chunks": st["total_chunks"],
                        "launches_in_graph": st["n_launches"], "tasks": st["n_tasks"],
                        "join_segments": st["n_segments"], "graph": bool(st["graph"]),
                        "accepted": int(got.sum()), "generate_s": round(gen_s, 1),
@@ -631,6 +635,10 @@ def main():
     ap.add_argument("--served-pool", type=int, default=2048)
     ap.add_argument("--batch-texts", type=int, default=10000)
     ap.add_argument("--batch-chunk-len", type=int, default=0, help="0 = autotune")
+    ap.add_argument("--batch-warps", type=int, default=0, help="warps per block of the batch's reach launches (0 = autotune)")
+    ap.add_argument("--batch-set-mode", type=int, default=0, help="batch set path: 0 autotune, 1 on, 2 off")
+    ap.add_argument("--no-batch-single", action="store_true",
+                    help="skip the one-text-per-launch comparison of the batched workload")
     ap.add_argument("--no-batch-per-re", action="store_true",
                     help="skip timing each batch RE alone on the concatenation of its texts")
     ap.add_argument("--text-bytes", type=int, default=None)
