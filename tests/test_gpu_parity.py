@@ -549,6 +549,7 @@ def test_two_byte_lane_copies_layout(mode):
     cases = ((textgen.regexp_family_re(5), textgen.regexp_family_text(200_003, seed=501), True),
              (textgen.regexp_family_re(7), textgen.regexp_family_text(300_001, seed=502), True),
              (textgen.C3_RE_ANYFIELD, textgen.c3_text(1 << 18, seed=503), True),
+             (textgen.C3_RE, textgen.c3_text(1 << 18, seed=507), True),          # k = 68: R = 4
              (textgen.C2_RE.replace("{20,60}", "{2,4}"), textgen.c2_text(300_007, seed=504), False))
     for re_src, x, dfa in cases:
         for c in (1, 7, 1000, 4099):
