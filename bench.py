@@ -536,31 +536,55 @@ def measure_served(args, lib, torch, dev, rank, rates, seconds):
     srv.bench_poisson(pslots, texts, rates[0], min(1.0, seconds), args.seed + 99)
     results = []
     total_mism = 0
+
+    def one_rate(rate, secs, seed, device_texts=None):
+        st0 = srv.stats()
+        recs, wall = srv.bench_poisson(pslots, texts, rate, secs, seed, device_texts=device_texts)
+        st1 = srv.stats()
+        lat = np.sort(recs["latency_us"] / 1e3)
+        slat = np.sort(recs["server_us"] / 1e3)
+        mism = int(np.count_nonzero((recs["status"] != 0) |
+                                    (recs["accept"].astype(bool) != want[recs["text"]])))
+        nb = st1["batches"] - st0["batches"]
+        hist = [a - b for a, b in zip(st1["batch_hist"], st0["batch_hist"])]
+        nbytes = int(lens[recs["text"]].sum())
+        return {"offered_rps": rate, "requests": int(len(recs)),
+                "achieved_rps": round(len(recs) / wall, 1),
+                "GBps": round(nbytes / wall / 1e9, 3),
+                "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "max_ms": round(float(lat[-1]), 3),
+                "server_p50_ms": round(float(np.percentile(slat, 50)), 3),
+                "server_p99_ms": round(float(np.percentile(slat, 99)), 3),
+                "batches": nb, "mean_batch": round(len(recs) / max(nb, 1), 1),
+                "batch_hist_log2": hist[:max([i + 1 for i, h in enumerate(hist) if h] or [1])],
+                "busy_retries": int(recs["busy_retries"].sum()),
+                "oracle_mismatches": mism}
+
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         for q, rate in enumerate(rates):
-            st0 = srv.stats()
-            recs, wall = srv.bench_poisson(pslots, texts, rate, seconds, args.seed + 7 + q)
-            st1 = srv.stats()
-            lat = np.sort(recs["latency_us"] / 1e3)
-            slat = np.sort(recs["server_us"] / 1e3)
-            mism = int(np.count_nonzero((recs["status"] != 0) |
-                                        (recs["accept"].astype(bool) != want[recs["text"]])))
-            total_mism += mism
-            nb = st1["batches"] - st0["batches"]
-            hist = [a - b for a, b in zip(st1["batch_hist"], st0["batch_hist"])]
-            nbytes = int(lens[recs["text"]].sum())
-            results.append({"offered_rps": rate, "requests": int(len(recs)),
-                            "achieved_rps": round(len(recs) / wall, 1),
-                            "GBps": round(nbytes / wall / 1e9, 3),
-                            "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                            "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                            "max_ms": round(float(lat[-1]), 3),
-                            "server_p50_ms": round(float(np.percentile(slat, 50)), 3),
-                            "server_p99_ms": round(float(np.percentile(slat, 99)), 3),
-                            "batches": nb, "mean_batch": round(len(recs) / max(nb, 1), 1),
-                            "batch_hist_log2": hist[:max([i + 1 for i, h in enumerate(hist) if h] or [1])],
-                            "busy_retries": int(recs["busy_retries"].sum()),
-                            "oracle_mismatches": mism})
+            results.append(one_rate(rate, seconds, args.seed + 7 + q))
+            total_mism += results[-1]["oracle_mismatches"]
+    # the same mix from device-resident texts (submitted in place: no client copy into the
+    # arena), at rates a host-copying client thread cannot offer: the server's own capacity
+    dev_results = []
+    dev_rates = [int(r) for r in args.served_device_rates.split(",") if r]
+    if dev_rates:
+        offs = np.zeros(len(texts), dtype=np.int64)
+        pos = 0
+        for i, x in enumerate(texts):
+            offs[i] = pos
+            pos = (pos + x.size + 15) & ~15
+        hbuf = np.zeros(max(pos, 16), np.uint8)
+        for o, x in zip(offs, texts):
+            hbuf[o:o + x.size] = x
+        dpool = torch.from_numpy(hbuf).to(dev)
+        dtexts = [(dpool.data_ptr() + int(o), int(x.size)) for o, x in zip(offs, texts)]
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk_dev:
+            for q, rate in enumerate(dev_rates):
+                dev_results.append(one_rate(rate, args.served_device_seconds, args.seed + 71 + q, dtexts))
+                total_mism += dev_results[-1]["oracle_mismatches"]
+        del dpool
     stats = srv.stats()
     srv.close()
     # one text per launch on the same request mix: copy, recognise, read the bit, one by one
@@ -580,6 +604,8 @@ def measure_served(args, lib, torch, dev, rank, rates, seconds):
     dt1 = time.perf_counter() - t0
     single = {"requests": len(pin), "GBps": round(nb1 / dt1 / 1e9, 3), "rps": round(len(pin) / dt1, 1)}
     return {"rates": results, "seconds_per_rate": seconds, "single_text_per_launch": single,
+            "device_texts": ({"rates": dev_results, "seconds_per_rate": args.served_device_seconds,
+                              "clocks": clk_dev.summary()} if dev_results else None),
             "config": {"workload": f"served: Poisson arrivals over {len(res)} resident REs, host texts "
                                    f"lognormal median 64 KiB sigma 1 (max 16 MiB), {seconds} s per rate",
                        "pool_texts": len(texts), "pool_mean_bytes": int(lens.mean()),
@@ -587,7 +613,8 @@ def measure_served(args, lib, torch, dev, rank, rates, seconds):
                        "device_budget": args.served_budget or None,
                        "chunk_len": args.batch_chunk_len or "adaptive (1-8 KiB per batch)",
                        "client": "ridfa_bench_served_poisson (C, open loop)"},
-            "oracle_check": {"requests": int(sum(r["requests"] for r in results)), "mismatches": total_mism,
+            "oracle_check": {"requests": int(sum(r["requests"] for r in results + dev_results)),
+                             "mismatches": total_mism,
                              "pool_oracle_s": round(oracle_s, 1)},
             "server_stats": stats, "clocks": clk.summary()}
 
@@ -604,6 +631,7 @@ def run_served(args, lib, torch, dev, rank):
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
                 "data": "synthetic", "config": cfg,
                 "rates": r["rates"], "single_text_per_launch": r["single_text_per_launch"],
+                "device_texts": r["device_texts"],
                 "oracle_check": r["oracle_check"], "server_stats": r["server_stats"], "clocks": r["clocks"],
                 "e2e": {"value": ref["GBps"], "unit": "GB/s",
                         "h2d_bytes_per_step": r["config"]["pool_mean_bytes"], "d2h_bytes_per_step": 1},
@@ -623,6 +651,9 @@ def main():
     ap.add_argument("--served-seconds", type=float, default=60.0,
                     help="--workload served: seconds of arrivals per rate (the configured 60 s)")
     ap.add_argument("--served-ref-rate", type=int, default=10000)
+    ap.add_argument("--served-device-rates", default="100000,200000,400000",
+                    help="rates also offered from device-resident texts (the server's own capacity); empty to skip")
+    ap.add_argument("--served-device-seconds", type=float, default=2.0)
     ap.add_argument("--served-budget", type=int, default=0,
                     help="server device budget in bytes (tables + texts + scratch; 0 = none)")
     ap.add_argument("--no-batched", action="store_true",

@@ -513,8 +513,10 @@ void ridfa_server_destroy(ridfa_server *srv);
 
 /* Open-loop Poisson load generator for a server (a measurement client; the paper has no
  * counterpart).  Arrivals at rate_rps for `seconds` (exponential gaps, seeded); each arrival
- * submits a uniformly chosen text of the caller's pool (host texts, copied into the arena) with
- * its program slot, retrying while the server answers E_BUSY, and polls results in between.
+ * submits a uniformly chosen text of the caller's pool with its program slot and submit_flags
+ * (0: host texts, copied into the arena; RIDFA_SUBMIT_DEVICE_TEXT: device texts, read in place,
+ * so that the client's copies do not limit the rate), retrying while the server answers E_BUSY,
+ * and polls results in between.
  * Latency of a request = (submit time - scheduled arrival) + the server's submit-to-result time,
  * so a client or server that falls behind is charged for it.  Runs on the calling thread and
  * returns when every request's result has been polled.
@@ -535,7 +537,7 @@ int ridfa_bench_served_poisson(ridfa_server *srv, const uint32_t *prog_slots,
                                const uint8_t *const *texts, const uint64_t *lens, uint32_t n_texts,
                                double rate_rps, double seconds, uint64_t seed,
                                ridfa_loadgen_record *out, uint32_t cap, uint32_t *n_out,
-                               double *wall_s);
+                               double *wall_s, uint32_t submit_flags);
 
 /* Roofline microbenchmarks (diagnostics; the paper has no counterpart).  Both allocate a 4-byte
  * sink and synchronise the current device.

@@ -458,7 +458,7 @@ _decl("ridfa_server_get_stats", _c.c_int, [_vp, _c.POINTER(ServerStats)])
 _decl("ridfa_server_destroy", None, [_vp])
 _decl("ridfa_bench_served_poisson", _c.c_int, [_vp, _vp, _vp, _vp, _u32, _c.c_double, _c.c_double,
                                                 _c.c_uint64, _c.POINTER(LoadgenRecord), _u32,
-                                                _c.POINTER(_u32), _c.POINTER(_c.c_double)])
+                                                _c.POINTER(_u32), _c.POINTER(_c.c_double), _u32])
 
 
 class Server:
@@ -522,19 +522,28 @@ class Server:
     def drain(self, timeout_ms=60_000):
         _check(_lib.ridfa_server_drain(self, int(timeout_ms)), "ridfa_server_drain")
 
-    def bench_poisson(self, prog_slots, texts, rate_rps, seconds, seed):
+    def bench_poisson(self, prog_slots, texts, rate_rps, seconds, seed, device_texts=None):
         """ridfa_bench_served_poisson over a pool of host texts (contiguous uint8 numpy arrays,
-        one program slot each).  Returns (records as a structured numpy array, wall seconds)."""
-        n = len(texts)
-        bufs = [np.ascontiguousarray(t, dtype=np.uint8) for t in texts]
-        ptrs = (_vp * n)(*[b.ctypes.data if b.size else None for b in bufs])
-        lens = (_c.c_uint64 * n)(*[int(b.size) for b in bufs])
+        one program slot each), or of device texts (device_texts: (pointer, length) pairs, read in
+        place).  Returns (records as a structured numpy array, wall seconds)."""
+        if device_texts is not None:
+            n = len(device_texts)
+            bufs = []
+            ptrs = (_vp * n)(*[int(p) if ln else None for p, ln in device_texts])
+            lens = (_c.c_uint64 * n)(*[int(ln) for _, ln in device_texts])
+            flags = RIDFA_SUBMIT_DEVICE_TEXT
+        else:
+            n = len(texts)
+            bufs = [np.ascontiguousarray(t, dtype=np.uint8) for t in texts]
+            ptrs = (_vp * n)(*[b.ctypes.data if b.size else None for b in bufs])
+            lens = (_c.c_uint64 * n)(*[int(b.size) for b in bufs])
+            flags = 0
         slots = (_u32 * n)(*[int(p) for p in prog_slots])
         cap = int(rate_rps * seconds * 1.5) + 1000
         recs = (LoadgenRecord * cap)()
         n_out, wall = _u32(), _c.c_double()
         _check(_lib.ridfa_bench_served_poisson(self, slots, ptrs, lens, n, float(rate_rps), float(seconds),
-                                               int(seed), recs, cap, _c.byref(n_out), _c.byref(wall)),
+                                               int(seed), recs, cap, _c.byref(n_out), _c.byref(wall), flags),
                "ridfa_bench_served_poisson")
         out = np.frombuffer(recs, dtype=np.dtype([("text", "<u4"), ("status", "<i4"), ("accept", "<u4"),
                                                   ("busy_retries", "<u4"), ("latency_us", "<f8"),

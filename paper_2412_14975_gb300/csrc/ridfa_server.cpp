@@ -597,7 +597,7 @@ extern "C" int ridfa_bench_served_poisson(ridfa_server *S, const uint32_t *prog_
                                           const uint8_t *const *texts, const uint64_t *lens, uint32_t n_texts,
                                           double rate_rps, double seconds, uint64_t seed,
                                           ridfa_loadgen_record *out, uint32_t cap, uint32_t *n_out,
-                                          double *wall_s) {
+                                          double *wall_s, uint32_t submit_flags) {
     using ridfa::Clock;
     if (!S || !prog_slots || !texts || !lens || !n_texts || !(rate_rps > 0) || !(seconds > 0) || !out ||
         !n_out)
@@ -645,7 +645,7 @@ extern "C" int ridfa_bench_served_poisson(ridfa_server *S, const uint32_t *prog_
         if (next < n && now_s() >= sched[next]) {
             const uint32_t j = which[next];
             uint64_t id = 0;
-            const int e = ridfa_server_submit(S, prog_slots[j], texts[j], lens[j], 0, &id);
+            const int e = ridfa_server_submit(S, prog_slots[j], texts[j], lens[j], submit_flags, &id);
             if (e == RIDFA_OK) {
                 submit_s[next] = now_s();
                 of_req.emplace(id, next);

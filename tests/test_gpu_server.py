@@ -215,3 +215,28 @@ def test_served_poisson_load_generator():
         st = srv.stats()
         assert st["completed"] == len(recs)
         assert sum(st["batch_hist"]) == st["batches"] and sum(st["batch_hist"][1:]) > 0
+
+
+def test_served_poisson_device_texts():
+    """The load generator on device-resident texts (submitted in place, no arena copy): every
+    request of an open-loop run gets a result equal to the oracle's."""
+    work = [(r, x) for r, x in workload(8, 61) if x.size]
+    expect = np.array([want(r, x) for r, x in work])
+    progs = [lib.ridfa_compile(r) for r in RES]
+    offs, pos = [], 0
+    for _, x in work:
+        offs.append(pos)
+        pos = (pos + x.size + 15) & ~15
+    buf = np.zeros(max(pos, 16), np.uint8)
+    for o, (_, x) in zip(offs, work):
+        buf[o:o + x.size] = x
+    d = torch.from_numpy(buf).to("cuda:0")
+    dev = [(d.data_ptr() + o, x.size) for o, (_, x) in zip(offs, work)]
+    with lib.Server(n_streams=3, arena_bytes=1 << 20) as srv:
+        slots = [srv.add_program(p) for p in progs]
+        recs, wall = srv.bench_poisson([slots[r] for r, _ in work], None, rate_rps=50000, seconds=0.4,
+                                       seed=12, device_texts=dev)
+        assert 16000 <= len(recs) <= 24000
+        assert (recs["status"] == 0).all()
+        assert np.array_equal(recs["accept"].astype(bool), expect[recs["text"]])
+        assert srv.stats()["completed"] == len(recs)
