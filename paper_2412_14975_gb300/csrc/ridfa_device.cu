@@ -566,7 +566,8 @@ struct LookbackArgs {
 constexpr int kLbRegs = 4;         // states per lane and pass of the look-back kernel
 
 // Every state x in [s0, s0 + 32*kLbRegs) run over text[w, e) (the warp in lockstep, all lanes on
-// the same byte); the live end states, in the policy's encoding, in s[].
+// the same byte); the live end states, in the policy's encoding, in s[].  With a two-byte table a
+// lane's states take each pair of bytes in one lookup through the pair's column.
 template <class LUT>
 __device__ __forceinline__ void run_all_states(const LUT &T, const Automaton &A, const uint8_t *text, uint64_t w,
                                                uint64_t e, uint32_t s0, uint32_t lane, uint32_t dead,
@@ -578,6 +579,13 @@ __device__ __forceinline__ void run_all_states(const LUT &T, const Automaton &A,
     }
     for (uint64_t q = w; q < e;) {
         const uint64_t stop = min(e, q + 8);
+        if constexpr (has_pairs<LUT>::value) {
+            for (; q + 1 < stop; q += 2) {
+                const uint32_t pc = T.pair_col(T.cls_of(__ldg(text + q)), T.cls_of(__ldg(text + q + 1)));
+#pragma unroll
+                for (int r = 0; r < kLbRegs; ++r) s[r] = T.next_pc(s[r], pc);
+            }
+        }
         for (; q < stop; ++q) {
             const uint32_t c = T.cls_of(__ldg(text + q));
 #pragma unroll
@@ -591,7 +599,7 @@ __device__ __forceinline__ void run_all_states(const LUT &T, const Automaton &A,
 }
 
 template <class LUT>
-__global__ void __launch_bounds__(512, 1) rid_lookback_kernel(LookbackArgs p, int table_in_smem) {
+__global__ void __launch_bounds__(512, 2) rid_lookback_kernel(LookbackArgs p, int table_in_smem) {
     extern __shared__ __align__(128) uint8_t smem[];
     const Automaton &A = p.A;
     LUT T;
@@ -823,8 +831,12 @@ cudaError_t piece_dispatch(const ReachArgs &a, const ReachPlan &pl, int sms, cud
     }
 }
 
-// Launch the look-back kernel: its work is latency-bound lockstep runs, so it takes the compact
-// table (small, leaving room for many warps) whatever layout the reach launch uses.
+// Launch the look-back kernel: its work is latency-bound lockstep runs, so it takes a compact
+// table (small, leaving room for many warps) whatever layout the reach launch uses: the two-byte
+// one where it fits (each lane steps 4 states over every byte pair through one column; the
+// regexp family k = 9 at 4,096 chunks 522 -> 616 GB/s, k = 7 1,228 -> 1,245), else the one-byte
+// one.  Two blocks of 512 threads an SM (64 registers: at 70 the two-byte kernel ran one block an
+// SM and lost its gain).
 template <class LUT>
 cudaError_t lookback_one(const LookbackArgs &a, int sms, size_t smem, int tis, cudaStream_t st) {
     auto kern = rid_lookback_kernel<LUT>;
@@ -841,6 +853,8 @@ cudaError_t lookback_one(const LookbackArgs &a, int sms, size_t smem, int tis, c
 
 cudaError_t lookback_dispatch(const LookbackArgs &a, int sms, cudaStream_t st) {
     const size_t limit = static_cast<size_t>(smem_optin_limit()) - 1024;
+    if (LutPairC::fits(a.A) && LutPairC::smem_bytes(a.A) <= limit / 2)
+        return lookback_one<LutPairC>(a, sms, LutPairC::smem_bytes(a.A), 0, st);
     if (LutPlain::fits(a.A) && LutPlain::smem_bytes(a.A) <= limit)
         return lookback_one<LutPlain>(a, sms, LutPlain::smem_bytes(a.A), 0, st);
     const size_t flat = LutFlat::smem_bytes(a.A);
@@ -1125,7 +1139,11 @@ int recognize_impl(const ridfa_program *P, bool use_dfa, const uint8_t *d_text, 
         const uint64_t fill = lb_able ? 4 : groups == 1 ? 2 : 4 * groups;
         if (spc < 2 && c * fill <= lanes) {
             const uint64_t plen = piece_req >= 64 ? piece_req : kManyPieceLen;
-            spc = std::min<uint64_t>(lanes / c, len / (c * plen));
+            // automata whose runs stay apart (the compile-time hint) run on the set path, at most
+            // 16 warps a block and one block an SM: one piece per lane of that one round (the
+            // codon RE at 4,096 chunks: 155,648 pieces 535 GB/s, 77,824 pieces 776)
+            const uint64_t plimit = lb_able && !H.merges ? static_cast<uint64_t>(sms) * 16 * 32 : lanes;
+            spc = std::min<uint64_t>(plimit / c, len / (c * plen));
         }
         // the piece functions take pieces * P * 2 bytes of scratch: at most kMaxPieceBytes
         spc = std::min<uint64_t>(spc, kMaxPieceBytes / (c * NS * 2));
