@@ -326,9 +326,9 @@ int ridfa_recognize_nfa(const ridfa_program *prog, const uint8_t *d_text, size_t
  *   ridfa_recognize).  Nothing is synchronised.
  * Limits: the tables plus 4 bytes per chunk plus about 133 KiB of join scratch must fit in the
  * array, otherwise RIDFA_E_TOO_LARGE and nothing is launched.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  The address is kept for the life of the
- * process, so the library must not be used across a cudaDeviceReset of that device.  The
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) and
+ * keeps it for the life of the process, so the library must not be used across a
+ * cudaDeviceReset of that device.  The
  * device status word (the join's consistency check, E_STATE on ridfa_recognize) is not reported
  * by this call, which returns once its work is queued.  Every call copies the program's tables into
  * the array and clears the counters the join needs; the array keeps the last call's contents.
