@@ -1008,7 +1008,10 @@ int plan_reach(const Automaton &A, const ridfa_tuning *tuning, const uint8_t *te
     // Automata whose table is too large to replicate are the ones whose runs stay apart: there a
     // lane finishes all of its chunk's runs together (measured on the codon RE: 1.21x; on
     // replicated-table workloads the 512-thread cap of that variant cost 8-13%).
-    const bool many_runs = mode == kModePlain || mode == kModeFlat || mode == kModeRep16x4C || mode == kModePairC;
+    // (the one-byte compact table of an automaton whose runs merge -- too large for any two-byte
+    // form, e.g. the regexp family at k = 11 -- keeps one run per lane)
+    const bool many_runs = (mode == kModePlain && !A.merges) || mode == kModeFlat || mode == kModeRep16x4C ||
+                           mode == kModePairC;
     if (text_path == 0)
         pl.path = !aligned ? kPathGlobal
                   : !w_coop ? kPathGlobal
