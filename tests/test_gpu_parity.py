@@ -648,3 +648,6 @@ def test_planner_choices():
     assert p["table_mode"] == 1, p
     p = plan_of(textgen.C3_RE, textgen.c3_text(1 << 20, seed=607), 4)
     assert p["pieces"] == 1, p
+    with pytest.raises(lib.RidfaError) as e:             # no call on this device yet
+        lib.ridfa_last_plan(lib.ridfa_compile(textgen.C1_RE))
+    assert e.value.code == -1
