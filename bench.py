@@ -891,7 +891,8 @@ def main():
         rc = lib.ridfa_count_transitions(prog, hx, c)
         work = {"rid_w_conv_per_byte": round(rc["w_conv"] / n, 5),
                 "rid_w_paper_per_byte": round(rc["w_paper"] / n, 5),
-                "rid_runs": rc["runs"], "rid_dead_runs": rc["dead_runs"]}
+                "rid_runs": rc["runs"], "rid_dead_runs": rc["dead_runs"],
+                "rid_converge_hist_log2": rc["converge_hist"]}
         if info["n_dfa_states"]:
             dc = lib.ridfa_count_transitions(prog, hx, c, dfa=True)
             work.update({"dfa_w_conv_per_byte": round(dc["w_conv"] / n, 5),

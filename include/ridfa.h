@@ -138,8 +138,10 @@ typedef struct {
  * (incremental powerset N(q0) u N(q1) u ..., Sec. 3.1), Nerode partition and delegation
  * (Sec. 3.4), byte classes, uint16 transition tables; optionally the minimal DFA.  Device tables
  * are uploaded on first use by a recognize call (so this works without a GPU).
- * opts may be NULL (minimize_interface = 1, build_dfa = 1, max_states = 65534).
- * Errors: E_ARG, E_SYNTAX, E_TOO_MANY_STATES, E_NOMEM.  *out is set only on success. */
+ * opts may be NULL (minimize_interface = 1, build_dfa = 1, max_states = 65534).  Every table
+ * index the kernels compute unchecked is verified on the host before the program is returned.
+ * Errors: E_ARG, E_SYNTAX, E_TOO_MANY_STATES, E_NOMEM, E_STATE (a table failed that check: an
+ * internal error).  *out is set only on success. */
 int ridfa_compile(const char *re, size_t re_len, const ridfa_compile_opts *opts,
                   ridfa_program **out);
 
@@ -223,6 +225,11 @@ typedef struct {
                            merged: distinct live states summed over positions */
     uint64_t runs;      /* runs started: 1 + (n_chunks - 1) * k */
     uint64_t dead_runs; /* runs that met the undefined move before their chunk end */
+    uint64_t converge_hist[16]; /* chunks 2..c by the bytes read until their runs leave at most
+                           one live state (convergence, Sec. 5; merged runs, dead runs dropped):
+                           bucket 0 for 0 or 1 byte, bucket b for 2^b .. 2^(b+1) - 1 bytes
+                           (b <= 14), bucket 15 for chunks still holding two or more live states
+                           at their end.  Zero for which = 2. */
 } ridfa_transition_counts;
 
 /* h_text: host pointer to len bytes; 1 <= n_chunks <= len; n_threads host threads over the

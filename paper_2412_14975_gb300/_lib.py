@@ -583,7 +583,7 @@ class Server:
 # ------------------------------------------------------------------------------ diagnostics
 class TransitionCounts(_c.Structure):
     _fields_ = [("w_paper", _c.c_uint64), ("w_conv", _c.c_uint64), ("runs", _c.c_uint64),
-                ("dead_runs", _c.c_uint64)]
+                ("dead_runs", _c.c_uint64), ("converge_hist", _c.c_uint64 * 16)]
 
 
 _decl("ridfa_count_transitions", _c.c_int, [_vp, _c.c_int, _vp, _c.c_size_t, _u32, _u32,
@@ -592,8 +592,9 @@ _decl("ridfa_count_transitions", _c.c_int, [_vp, _c.c_int, _vp, _c.c_size_t, _u3
 
 def ridfa_count_transitions(prog, text, n_chunks, dfa=False, n_threads=0, nfa=False):
     """Host transition counts of the reach phase over a host text (bytes or uint8 array):
-    dict with w_paper, w_conv, runs, dead_runs; dfa=True for the all-states DFA comparator,
-    nfa=True for the NFA variant."""
+    dict with w_paper, w_conv, runs, dead_runs and converge_hist (16 log2 buckets of the bytes
+    until a chunk's runs leave one live state; the last: never); dfa=True for the all-states DFA
+    comparator, nfa=True for the NFA variant."""
     if isinstance(text, (bytes, bytearray)):
         buf = np.frombuffer(text, dtype=np.uint8)
     else:
@@ -602,7 +603,7 @@ def ridfa_count_transitions(prog, text, n_chunks, dfa=False, n_threads=0, nfa=Fa
     which = 2 if nfa else int(bool(dfa))
     _check(_lib.ridfa_count_transitions(prog, which, buf.ctypes.data if buf.size else None, buf.size,
                                         int(n_chunks), int(n_threads), _c.byref(out)), "ridfa_count_transitions")
-    return {f: getattr(out, f) for f, _ in out._fields_}
+    return {f: (list(getattr(out, f)) if f == "converge_hist" else getattr(out, f)) for f, _ in out._fields_}
 
 
 _decl("ridfa_cpu_recognize", _c.c_int, [_vp, _c.c_int, _vp, _c.c_size_t, _u32, _u32, _c.POINTER(_c.c_uint8)])

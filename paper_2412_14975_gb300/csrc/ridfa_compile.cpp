@@ -750,6 +750,33 @@ bool build_min_dfa(const ClassNfa &N, uint32_t cap, ridfa_program &P) {
     return true;
 }
 
+// Bounds of every table index the device kernels compute without checking: transitions and slot
+// states are states or the dead state n (whose row maps to itself), class numbers are below C,
+// the q0 slot is a slot, and every table has the size the kernels assume.  A failure is an
+// internal error of the construction above (never expected), reported as E_STATE.
+bool tables_in_bounds(const ridfa::HostAutomaton &A) {
+    const uint32_t n = A.n_states, C = A.n_classes;
+    if (C == 0 || C > 256 || n > RIDFA_MAX_STATES || A.k == 0 || A.q0_slot >= A.k) return false;
+    if (A.kw != (A.k + 31) / 32 || A.classmap.size() != 256 || A.final_flag.size() != n ||
+        A.trans.size() != static_cast<size_t>(n + 1) * C || A.slot_state.size() != A.k ||
+        A.ifmask.size() != static_cast<size_t>(n + 1) * A.kw || A.final_bits.size() < (n + 1 + 31) / 32)
+        return false;
+    for (uint8_t c : A.classmap)
+        if (c >= C) return false;
+    for (uint16_t t : A.trans)
+        if (t > n) return false;
+    for (uint32_t c = 0; c < C; ++c)
+        if (A.trans[static_cast<size_t>(n) * C + c] != n) return false;
+    for (uint16_t s : A.slot_state)
+        if (s >= n) return false;
+    for (uint32_t w = 0; w < A.kw; ++w)
+        if (A.ifmask[static_cast<size_t>(n) * A.kw + w] != 0) return false;
+    if (A.k % 32)
+        for (uint32_t p = 0; p <= n; ++p)
+            if (A.ifmask[static_cast<size_t>(p) * A.kw + A.kw - 1] >> (A.k % 32)) return false;
+    return true;
+}
+
 }  // namespace
 
 extern "C" int ridfa_compile(const char *re, size_t re_len, const ridfa_compile_opts *opts,
@@ -784,6 +811,10 @@ extern "C" int ridfa_compile(const char *re, size_t re_len, const ridfa_compile_
     } catch (...) {
         delete P;
         return RIDFA_E_NOMEM;
+    }
+    if (!tables_in_bounds(P->rid) || (P->has_dfa && !tables_in_bounds(P->dfa))) {
+        delete P;
+        return RIDFA_E_STATE;
     }
     *out = P;
     return RIDFA_OK;

@@ -21,7 +21,16 @@ namespace {
 
 struct Counts {
     uint64_t w_paper = 0, w_conv = 0, runs = 0, dead = 0;
+    uint64_t conv[16] = {};
 };
+
+// Bucket of a convergence distance (bytes read until at most one live state): 0 for 0 or 1,
+// b for 2^b .. 2^(b+1) - 1, at most 14.
+uint32_t conv_bucket(uint64_t bytes) {
+    uint32_t b = 0;
+    while (b < 14 && (bytes >> (b + 1)) != 0) ++b;
+    return b;
+}
 
 uint64_t chunk_at(uint64_t i, uint64_t len, uint64_t c) { return i * (len / c) + (i * (len % c)) / c; }
 
@@ -36,6 +45,7 @@ void count_range(const HostAutomaton &H, const uint8_t *text, uint64_t len, uint
     Counts k;
     for (uint64_t i = c_lo; i < c_hi; ++i) {
         const uint64_t b = chunk_at(i, len, c), e = chunk_at(i + 1, len, c);
+        uint64_t conv_at = UINT64_MAX;      // bytes read when at most one live state remained
         st.clear();
         mult.clear();
         if (i == 0) {
@@ -49,7 +59,9 @@ void count_range(const HostAutomaton &H, const uint8_t *text, uint64_t len, uint
             }
         }
         k.runs += st.size();
-        for (uint64_t p = b; p < e && !st.empty(); ++p) {
+        uint64_t p = b;
+        for (; p < e && !st.empty(); ++p) {
+            if (i > 0 && st.size() <= 1 && conv_at == UINT64_MAX) conv_at = p - b;
             const uint32_t cls = H.classmap[text[p]];
             k.w_conv += st.size();
             if (++gen == 0) {                      // stamp wrap-around: clear once
@@ -76,6 +88,10 @@ void count_range(const HostAutomaton &H, const uint8_t *text, uint64_t len, uint
             }
             st.swap(st2);
             mult.swap(mult2);
+        }
+        if (i > 0) {
+            if (conv_at == UINT64_MAX && st.size() <= 1) conv_at = p - b;
+            ++k.conv[conv_at == UINT64_MAX ? 15 : conv_bucket(conv_at)];
         }
     }
     *out = k;
@@ -159,6 +175,7 @@ extern "C" int ridfa_count_transitions(const ridfa_program *prog, int which, con
         r.w_conv += p.w_conv;
         r.runs += p.runs;
         r.dead_runs += p.dead;
+        for (int q = 0; q < 16; ++q) r.converge_hist[q] += p.conv[q];
     }
     *out = r;
     return RIDFA_OK;

@@ -66,7 +66,7 @@ def test_closed_forms_single_chunk_and_dead_runs():
     # a byte outside the alphabet kills every run: no transitions, one lookup per live state
     p = lib.ridfa_compile("(ab)*")
     r = lib.ridfa_count_transitions(p, b"zab", 1)
-    assert r == {"w_paper": 0, "w_conv": 1, "runs": 1, "dead_runs": 1}
+    assert r == {"w_paper": 0, "w_conv": 1, "runs": 1, "dead_runs": 1, "converge_hist": [0] * 16}
     # c = len: every chunk one byte; chunk 1 from {q0}, the others from each of the k slots
     k = p.info["k"]
     r = lib.ridfa_count_transitions(p, b"abab", 4)
@@ -163,7 +163,9 @@ def test_nfa_variant_counts_match_definition(re_name):
         for c in (1, 3, 40):
             b = chunk_boundaries(t.size, c)
             chunks = [bytes(t[b[i]:b[i + 1]]) for i in range(c)]
-            assert lib.ridfa_count_transitions(prog, t, c, nfa=True) == nfa_variant_counts(nfa, chunks)
+            got = lib.ridfa_count_transitions(prog, t, c, nfa=True)
+            assert got.pop("converge_hist") == [0] * 16
+            assert got == nfa_variant_counts(nfa, chunks)
 
 
 def test_nfa_variant_counts_refuse_large_nfa():
@@ -172,3 +174,65 @@ def test_nfa_variant_counts_refuse_large_nfa():
     with pytest.raises(lib.RidfaError) as e:
         lib.ridfa_count_transitions(prog, textgen.c3_text(1000, seed=16), 4, nfa=True)
     assert e.value.code == -9          # E_UNSUPPORTED
+
+
+def converge_hist_by_definition(B, chunks):
+    """Histogram of the bytes each chunk (after the first) reads until at most one live state of
+    its runs from every interface slot remains, with the oracle's RI-DFA; bucket 15: never."""
+    hist = [0] * 16
+    for y in chunks[1:]:
+        live = set(B.slots[a] for a in range(B.k))
+        at = None
+        for t in range(len(y) + 1):
+            if len(live) <= 1:
+                at = t
+                break
+            if t < len(y):
+                live = {p for p in (B.step(s, y[t]) for s in live) if p is not UNDEF}
+        if at is None:
+            hist[15] += 1
+        else:
+            b = 0
+            while b < 14 and (at >> (b + 1)):
+                b += 1
+            hist[b] += 1
+    return hist
+
+
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_convergence_histogram_definite_automaton(k):
+    """(a|b)*a(a|b){k} is k+1-definite: from every slot, runs over any k+1 letters end in one state
+    and not before, so every chunk converges after exactly k + 1 bytes (bucket floor(log2(k+1)));
+    the histogram also equals its definition evaluated with the oracle's RI-DFA."""
+    re_src = textgen.regexp_family_re(k)
+    x = textgen.regexp_family_text(200_000, seed=40 + k)
+    prog = lib.ridfa_compile(re_src)
+    B = RidOracle(re_src).B
+    for c in (2, 64, 999):
+        h = lib.ridfa_count_transitions(prog, x, c)["converge_hist"]
+        want_bucket = (k + 1).bit_length() - 1
+        assert h[want_bucket] == c - 1 and sum(h) == c - 1, (k, c, h)
+        b = chunk_boundaries(x.size, c)
+        chunks = [bytes(x[b[i]:b[i + 1]]) for i in range(c)]
+        assert h == converge_hist_by_definition(B, chunks), (k, c)
+
+
+def test_convergence_histogram_reading_frames_and_record_lines():
+    """The codon RE's runs sit in three reading frames and never meet (every chunk in bucket 15),
+    the record lines' runs meet within 16 bytes; both equal the definition with the oracle."""
+    re2 = textgen.C2_RE.replace("{20,60}", "{2,4}")
+    x = textgen.c2_text(60_000, seed=50)
+    h = lib.ridfa_count_transitions(lib.ridfa_compile(re2), x, 100)["converge_hist"]
+    assert h[15] == 99, h
+    b = chunk_boundaries(x.size, 100)
+    assert h == converge_hist_by_definition(RidOracle(re2).B, [bytes(x[b[i]:b[i + 1]]) for i in range(100)])
+    y = textgen.c3_text(200_000, seed=51)
+    h = lib.ridfa_count_transitions(lib.ridfa_compile(textgen.C3_RE), y, 300)["converge_hist"]
+    assert sum(h[:4]) == 299 and h[15] == 0, h
+    b = chunk_boundaries(y.size, 300)
+    assert h == converge_hist_by_definition(RidOracle(textgen.C3_RE).B,
+                                            [bytes(y[b[i]:b[i + 1]]) for i in range(300)])
+    # the NFA variant reports no histogram
+    p1 = lib.ridfa_compile(textgen.C1_RE)
+    z = textgen.c1_text(5000, seed=52)
+    assert lib.ridfa_count_transitions(p1, z, 10, nfa=True)["converge_hist"] == [0] * 16
