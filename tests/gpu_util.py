@@ -4,8 +4,10 @@ import numpy as np
 
 def to_device(text):
     import torch
-    t = torch.from_numpy(np.ascontiguousarray(text, dtype=np.uint8))
-    return t.to("cuda:0")
+    a = np.ascontiguousarray(text, dtype=np.uint8)
+    if not a.flags.writeable:              # (torch warns on read-only arrays; copy those)
+        a = a.copy()
+    return torch.from_numpy(a).to("cuda:0")
 
 
 def run(lib, prog, d_text, n, c, dfa=False, tuning=None, with_maps=True):
