@@ -7,6 +7,7 @@ import pytest
 import textgen
 from oracle.recognizer import RidOracle
 from oracle.ridfa_sets import UNDEF, chunk_boundaries, chunk_mapping, rid_join
+from tests.gpu_util import to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +39,7 @@ def check(re_src, x, c):
     prog = lib.ridfa_compile(re_src, build_dfa=False)
     k = prog.info["k"]
     kw = (k + 31) // 32
-    d = torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+    d = to_device(x)
     maps = torch.empty((c, k), dtype=torch.int16, device="cuda:0")
     lib.ridfa_recognize(prog, d, x.size, c, d_chunk_maps=maps)
     ent = torch.full((c, kw), -1, dtype=torch.int32, device="cuda:0")

@@ -8,6 +8,7 @@ import pytest
 import textgen
 from oracle.recognizer import RidOracle, SerialRecognizer
 from tests.shard_util import oracle_summary, split_points, summaries_equal
+from tests.gpu_util import to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +49,7 @@ def test_shard_summaries_and_join():
             if trial % 2:
                 y, _ = textgen.mutate(x, rng, n_subs=1)
             want = ser.accepts(y)
-            d = torch.from_numpy(np.ascontiguousarray(y)).to("cuda:0")
+            d = to_device(y)
             n_shards = 1 + trial
             cuts = split_points(y.size, n_shards, rng)
             sums = []
